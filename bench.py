@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Throughput of the spline x-ray projector on one GB300.
+
+Workload: 512 x 512 cubic B-spline grid, fan beam with 720 views x 768 bins
+(dso 1000, dod 500), 30-ellipse seeded phantom.  One step is one pass of the
+whole hot path over that batch: line setup, footprint tables, forward
+projection and adjoint, each a call of the C ABI (spline_plan_prepare,
+spline_plan_fwd, spline_plan_adj).  value = lines x steps / time, in Mrays/s
+(one ray counted once per forward+adjoint pair).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (launched by torch.distributed.run) every rank runs its own
+instance (independent replicas, weak scaling); value is the sum over ranks
+divided by the slowest rank's time.  --impl reference times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s fwd+adj at 512² cubic fan-beam (% roofline); learned-vs-cold CG time to 1e-4"
+UNIT = "Mrays/s"
+WORKLOAD = "fan512_cubic"
+FP32_LANES_PER_SM = 128
+FLOPS_PER_PAIR = lambda n: 2 * (2 * n + 3)   # noqa: E731  (2n+1 Horner FMAs, 1 offset, 1 accumulate)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.path = index, None, None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(n_gpus):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return dist.get_rank(), ws, local
+    return 0, 1, 0
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(wl, seconds_hint: float = 1.0):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the
+    workload and scale to the full job: forward on a random subset of lines,
+    adjoint on a random subset of nodes (pixel-driven over every line)."""
+    import numpy as np
+    import oracle
+    geo = wl.geometry
+    th, yy = oracle.lines_fan(geo.view_angle.astype(np.float64), geo.dso, geo.dod, geo.n_det,
+                              geo.det0, geo.ddet)
+    g = oracle.Grid(wl.n, wl.n, wl.degree, wl.h)
+    rng = np.random.default_rng(7)
+    nf = 6000
+    ridx = np.sort(rng.choice(th.size, nf, replace=False))
+    t0 = time.perf_counter()
+    oracle.forward(g, wl.coef, th[ridx], yy[ridx])
+    tf = time.perf_counter() - t0
+    p = rng.uniform(-1, 1, th.size)
+    npix = 160
+    pix = np.sort(rng.choice(wl.n * wl.n, npix, replace=False))
+    t0 = time.perf_counter()
+    oracle.adjoint_pixels(g, p, th, yy, pix)
+    ta = time.perf_counter() - t0
+    m = th.size
+    t_full = tf * m / nf + ta * (wl.n * wl.n) / npix
+    return {"value": m / t_full / 1e6, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"forward on {nf} of {m} lines ({tf:.2f} s), adjoint on {npix} of {wl.n * wl.n} nodes "
+                      f"({ta:.2f} s), scaled to the full job ({t_full:.0f} s)",
+            "seconds": tf + ta}
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    import workloads
+    wl = workloads.workload(WORKLOAD)
+    times = []
+    for k in range(args.warmup + args.steps):
+        cb = oracle_sample(wl)
+        if k >= args.warmup:
+            times.append(cb)
+    value = statistics.mean(c["value"] for c in times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * statistics.mean(c["seconds"] for c in times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": wl.n, "degree": wl.degree,
+                                            "geometry": "fan 720 views x 768 bins, dso 1000, dod 500",
+                                            "sample": "bounded sample per step, scaled to the full job"},
+            "cpu_baseline": {k: times[-1][k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU
+def run_ours(args, rank, ws, local):
+    import numpy as np
+    import torch
+
+    import paper_2503_20907_gb300 as sp
+    import workloads
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    props = torch.cuda.get_device_properties(dev)
+    wl = workloads.workload(WORKLOAD)
+    geo = wl.geometry
+    grid = sp.Grid(wl.n, wl.n, wl.degree, wl.h)
+    view = torch.from_numpy(geo.view_angle).to(dev)
+    lines = sp.Lines.fan(view, geo.dso, geo.dod, geo.n_det, geo.det0, geo.ddet)
+    M = lines.m
+    coef = torch.from_numpy(wl.coef).to(dev)
+    sino = torch.empty(M, device=dev)
+    back = torch.empty(wl.n, wl.n, device=dev)
+    plan = sp.Plan(grid, lines, prepare=True)
+    pairs = int(sp.spline_visited(grid, lines).to(torch.int64).sum().item())
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        plan.prepare(stream)
+        if ev: ev[1].record(stream)
+        plan.fwd(coef, sino, stream)
+        if ev: ev[2].record(stream)
+        plan.adj(sino, back, stream)
+        if ev: ev[3].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))          # L2 flush between timed steps (outside the events)
+        step(evs[k])
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    prep = [e[0].elapsed_time(e[1]) for e in evs]
+    fwd = [e[1].elapsed_time(e[2]) for e in evs]
+    adj = [e[2].elapsed_time(e[3]) for e in evs]
+    tot = sum(e[0].elapsed_time(e[3]) for e in evs) / 1000.0
+    tmax = allreduce_max(tot, ws)
+
+    # end to end through the public API with host buffers
+    coef_h = torch.from_numpy(wl.coef).pin_memory()
+    view_h = torch.from_numpy(geo.view_angle).pin_memory()
+    sino_h = torch.empty(M, dtype=torch.float32).pin_memory()
+    back_h = torch.empty(wl.n, wl.n, dtype=torch.float32).pin_memory()
+    coef_d = torch.empty_like(coef)
+
+    def e2e_step():
+        coef_d.copy_(coef_h, non_blocking=True)
+        view.copy_(view_h, non_blocking=True)
+        plan.prepare(stream)
+        plan.fwd(coef_d, sino, stream)
+        plan.adj(sino, back, stream)
+        sino_h.copy_(sino, non_blocking=True)
+        back_h.copy_(back, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    e2e_t = allreduce_max(sum(e_ms) / 1000.0, ws)
+    h2d = coef_h.numel() * 4 + view_h.numel() * 4
+    d2h = sino_h.numel() * 4 + back_h.numel() * 4
+
+    if rank != 0:
+        return
+    value = ws * M * args.steps / tmax / 1e6
+    fwd_ms, adj_ms, prep_ms = statistics.mean(fwd), statistics.mean(adj), statistics.mean(prep)
+    dom_name, dom_ms = ("spline_fwd", fwd_ms) if fwd_ms >= adj_ms else ("spline_adj", adj_ms)
+    flops = FLOPS_PER_PAIR(wl.degree) * pairs
+    achieved = flops / (dom_ms / 1000.0) / 1e12
+    max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * tmax / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": wl.n, "degree": wl.degree,
+                   "geometry": "fan 720 views x 768 bins, dso 1000, dod 500", "lines": M,
+                   "phantom": "30 seeded ellipses", "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "stage_ms": {"prepare": prep_ms, "fwd": fwd_ms, "adj": adj_ms},
+        "pairs_per_direction": pairs,
+        "basis_evals_per_s": 2 * pairs * args.steps / (tot) if tot > 0 else None,
+        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
+                                    f"x 2 x {max_mhz:.0f} MHz max SM clock",
+                     "flops_per_pair": FLOPS_PER_PAIR(wl.degree)},
+        "e2e": {"value": M * args.steps / e2e_t / 1e6 * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "wall_s": wall,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(wl)
+        cb.pop("seconds", None)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

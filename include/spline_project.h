@@ -1,0 +1,186 @@
+/*
+ * spline_project.h -- C ABI of the GB300 spline x-ray projector.
+ *
+ * The library computes the x-ray transform of an image written as a sum of
+ * shifted tensor-product B-splines, and its exact adjoint (backprojection),
+ * over any list of lines ("Generalized Ray Tracing with Basis Functions for
+ * Tomographic Projections", arXiv 2503.20907).
+ *
+ * Image model (eq. def_f, eq. xrtbasis, Sec. III.C):
+ *   f(x) = sum_k c_k phi((x - x_k)/h),  phi(x1, x2) = beta^n(x1) beta^n(x2),
+ *   node k = (i, j) at x_k = (cx + (i - (nx-1)/2) h, cy + (j - (ny-1)/2) h),
+ *   beta^n the centred B-spline of degree n = 0..3.
+ * Lines (eq. rayparam): {t theta + y theta^perp}, theta = (cos, sin),
+ *   theta^perp = (sin, -cos).
+ * Forward (eq. xray with eq. xrtbasis, discretised operator of Sec. IV.A):
+ *   p_m = h * sum_k c_k phi_{theta_m}((y_m - <x_k, theta_m^perp>)/h)
+ * Adjoint (Sec. II.B, "exactly matched"):
+ *   c'_k = h * sum_m p_m phi_{theta_m}((y_m - <x_k, theta_m^perp>)/h)
+ * phi_theta is the exact x-ray transform of phi (Prop. 1, eq. xsa).
+ *
+ * Conventions shared by every entry point:
+ *   - Array pointers are DEVICE pointers owned by the caller; the library keeps
+ *     no reference to them after the call returns.
+ *   - Coefficient images are float32 [ny][nx], row j (x2) major, i (x1) fastest.
+ *   - Sinograms are float32 [m]; for the structured kinds the ray index is
+ *     view * n_det + bin (view-major, bin fastest).
+ *   - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) and runs asynchronously; the call returns after enqueueing.
+ *   - Argument errors detectable on the host return SP_EINVAL before anything
+ *     is enqueued.  A CUDA error returns SP_ECUDA.  sp_last_error() gives a
+ *     message for the last failing call on the calling thread.
+ *   - Internal workspace (per-line records and footprint tables) is cached per
+ *     device and grows on demand; sp_release_workspace() frees it.  Calls on
+ *     one device must not overlap from several host threads.
+ *   - Lines that miss the support of every basis give 0.  Lines with
+ *     non-finite parameters give unspecified values.
+ */
+#ifndef SPLINE_PROJECT_H
+#define SPLINE_PROJECT_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sp_status {
+    SP_OK = 0,
+    SP_EINVAL = -1,        /* invalid argument (checked on the host) */
+    SP_ENOMEM = -2,        /* device allocation of the workspace failed */
+    SP_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed */
+    SP_EUNSUPPORTED = -5   /* valid request that this build does not support */
+} sp_status;
+
+/* Coefficient grid: nx x ny nodes, spacing h > 0, centre (cx, cy), degree n. */
+typedef struct sp_grid {
+    int32_t nx, ny;        /* 1 <= nx, ny <= 16384 */
+    int32_t degree;        /* spline degree n, 0..3 */
+    int32_t reserved;      /* must be 0 */
+    float h;               /* grid spacing */
+    float cx, cy;          /* grid centre */
+} sp_grid;
+
+typedef enum sp_lines_kind {
+    SP_LINES_THETA_Y = 0,  /* line m = (theta[m], y[m]) (eq. rayparam) */
+    SP_LINES_POINTS = 1,   /* infinite line through src[m] and dst[m] */
+    SP_LINES_PARALLEL = 2, /* line (v, j) = (view[v], det0 + j*ddet) */
+    SP_LINES_FAN = 3       /* flat-detector fan beam, see below */
+} sp_lines_kind;
+
+/*
+ * A line list.  Fields not used by `kind` are ignored.
+ *
+ * SP_LINES_FAN: for view v with source angle beta = view[v], the source is at
+ * dso*(cos beta, sin beta); the detector is the line through
+ * -dod*(cos beta, sin beta) with direction (-sin beta, cos beta), and bin j is
+ * centred at offset det0 + j*ddet along it.  Ray (v, j) joins the source to
+ * the centre of bin j.  (The paper's fan geometry is not specified in closed
+ * form; this is the flat-detector fan of its experiments, Sec. IV.B/IV.C.)
+ */
+typedef struct sp_lines {
+    int32_t kind;          /* sp_lines_kind */
+    int32_t n_view;        /* PARALLEL, FAN: number of views (>= 1) */
+    int32_t n_det;         /* PARALLEL, FAN: bins per view (>= 1) */
+    int32_t reserved;      /* must be 0 */
+    int64_t m;             /* THETA_Y, POINTS: number of lines (>= 0);
+                              PARALLEL, FAN: 0 or n_view*n_det */
+    const float *theta;    /* THETA_Y: device [m] angles (radians) */
+    const float *y;        /* THETA_Y: device [m] offsets */
+    const float *src;      /* POINTS: device [m][2] first point */
+    const float *dst;      /* POINTS: device [m][2] second point (!= src) */
+    const float *view;     /* PARALLEL: device [n_view] line angles;
+                              FAN: device [n_view] source angles */
+    float det0, ddet;      /* PARALLEL, FAN: offset of bin 0 and bin spacing */
+    float dso, dod;        /* FAN: source-origin and origin-detector distances */
+} sp_lines;
+
+/* Number of lines described by `lines` (-1 if the description is invalid). */
+int64_t sp_lines_count(const sp_lines *lines);
+
+/*
+ * Forward projection (Sec. II, Algorithm 2's output for every line):
+ *   sino[m] = h * sum_k coef[k] * phi_{theta_m}((y_m - <x_k, theta_m^perp>)/h).
+ * coef: device float [ny][nx] (read only).  sino: device float [m] (written).
+ */
+sp_status spline_project_fwd(const sp_grid *grid, const float *coef,
+                             const sp_lines *lines, float *sino, void *stream);
+
+/*
+ * Adjoint (backprojection), the exact transpose of spline_project_fwd
+ * (Sec. II.B): coef_out[k] = h * sum_m sino[m] * phi_{theta_m}(...).
+ * sino: device float [m] (read only).  coef_out: device float [ny][nx],
+ * overwritten (not accumulated into).
+ */
+sp_status spline_project_adj(const sp_grid *grid, const float *sino,
+                             const sp_lines *lines, float *coef_out, void *stream);
+
+/*
+ * Line setup on its own (the first step of the hot path, eq. rayparam):
+ * writes theta_out[m] and y_out[m] (device float) for every line, with
+ * theta in (-pi, pi] the direction angle and y = <P, theta^perp> for a point
+ * P of the line.  Either output may be NULL.
+ */
+sp_status spline_lines_expand(const sp_lines *lines, float *theta_out, float *y_out,
+                              void *stream);
+
+/*
+ * The footprint phi_theta(yt) on the unit grid (Prop. 1, eq. xsa) as the
+ * projector evaluates it: out[r] = phi_{theta[r]}(yt[r]) for r < count.
+ * theta, yt, out: device float [count].  For testing and inspection.
+ */
+sp_status spline_footprint_eval(int32_t degree, int64_t count, const float *theta,
+                                const float *yt, float *out, void *stream);
+
+/*
+ * The nonzero (line, node) pairs the projector visits, i.e. the pairs with
+ * |y~| < w, w = (n+1)(|cos|+|sin|)/2 (closed for degree 0 along an axis).
+ * counts: device int32 [m], written with the number of pairs of each line.
+ * If offsets != NULL (device int64 [m], exclusive prefix sums of counts) and
+ * nodes != NULL, nodes[offsets[m] ...] receives each line's node indices
+ * j*nx + i, in the projector's own order (unordered within a line).
+ */
+sp_status spline_visited(const sp_grid *grid, const sp_lines *lines, int32_t *counts,
+                         const int64_t *offsets, int32_t *nodes, void *stream);
+
+/*
+ * Plans.  A plan keeps the per-line records and footprint tables of one
+ * (grid, lines) pair in its own device memory, so that repeated projections
+ * (iterative reconstruction, autograd) skip the setup.  The steps of one pass
+ * of the projector are then separate calls:
+ *   spline_plan_prepare  line setup (eq. rayparam) and footprint tables
+ *                        (Prop. 1, eq. xsa);
+ *   spline_plan_fwd      forward projection (Algorithms 1-2);
+ *   spline_plan_adj      adjoint.
+ * spline_plan_create allocates (cudaMalloc on the current device) and copies
+ * the descriptors but enqueues no work; the device arrays that `lines` points
+ * to must stay valid until the last spline_plan_prepare on the plan has run.
+ * A plan is used on the device that was current at creation.  Calls on one
+ * plan must be ordered (same stream, or synchronised).
+ */
+typedef struct sp_plan sp_plan;
+
+sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan **plan);
+sp_status spline_plan_prepare(sp_plan *plan, void *stream);
+sp_status spline_plan_fwd(const sp_plan *plan, const float *coef, float *sino, void *stream);
+sp_status spline_plan_adj(const sp_plan *plan, const float *sino, float *coef_out, void *stream);
+/* Number of lines of the plan (-1 if plan is NULL). */
+int64_t spline_plan_lines(const sp_plan *plan);
+/* Free the plan and its device memory (synchronises the device first). */
+sp_status spline_plan_destroy(sp_plan *plan);
+
+/* Free the cached workspace of the current device (synchronises the device). */
+sp_status sp_release_workspace(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *sp_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t sp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPLINE_PROJECT_H */

@@ -1,0 +1,374 @@
+// C ABI of the spline x-ray projector (declared in include/spline_project.h):
+// argument checks, the cached per-device workspace and the order of the
+// kernels of one call (line setup, footprint tables, projection).
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+sp_status fail(sp_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+sp_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(SP_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+constexpr int kMaxDevices = 64;
+
+struct Workspace {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+std::mutex g_mu;
+Workspace g_ws[kMaxDevices];
+
+// Workspace of at least `bytes` on the current device.
+sp_status workspace(size_t bytes, void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(SP_EUNSUPPORTED, "device index too large");
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace &ws = g_ws[dev];
+    if (ws.bytes < bytes) {
+        if (ws.ptr) {
+            // earlier calls may still use it
+            e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            cudaFree(ws.ptr);
+            ws.ptr = nullptr;
+            ws.bytes = 0;
+        }
+        size_t grow = bytes + bytes / 4 + (1u << 20);
+        e = cudaMalloc(&ws.ptr, grow);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ws.ptr = nullptr;
+            return fail(SP_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+        }
+        ws.bytes = grow;
+    }
+    *out = ws.ptr;
+    return SP_OK;
+}
+
+bool finite(float v) { return std::isfinite(v); }
+
+sp_status check_grid(const sp_grid *g, spx::GridDev *out)
+{
+    if (!g) return fail(SP_EINVAL, "grid is NULL");
+    if (g->nx < 1 || g->ny < 1 || g->nx > 16384 || g->ny > 16384)
+        return fail(SP_EINVAL, "grid size must be in [1, 16384]");
+    if (g->degree < 0 || g->degree > 3) return fail(SP_EINVAL, "degree must be 0..3");
+    if (g->reserved != 0) return fail(SP_EINVAL, "grid.reserved must be 0");
+    if (!finite(g->h) || !(g->h > 0.f)) return fail(SP_EINVAL, "grid spacing h must be finite and > 0");
+    if (!finite(g->cx) || !finite(g->cy)) return fail(SP_EINVAL, "grid centre must be finite");
+    *out = spx::GridDev{g->nx, g->ny, g->degree, g->h, g->cx, g->cy};
+    return SP_OK;
+}
+
+int64_t count_lines(const sp_lines *L)
+{
+    if (!L || L->reserved != 0) return -1;
+    switch (L->kind) {
+    case SP_LINES_THETA_Y:
+    case SP_LINES_POINTS:
+        return L->m >= 0 ? L->m : -1;
+    case SP_LINES_PARALLEL:
+    case SP_LINES_FAN: {
+        if (L->n_view < 1 || L->n_det < 1) return -1;
+        int64_t m = (int64_t)L->n_view * (int64_t)L->n_det;
+        if (L->m != 0 && L->m != m) return -1;
+        return m;
+    }
+    default:
+        return -1;
+    }
+}
+
+sp_status check_lines(const sp_lines *L, spx::LinesDev *out)
+{
+    if (!L) return fail(SP_EINVAL, "lines is NULL");
+    if (L->reserved != 0) return fail(SP_EINVAL, "lines.reserved must be 0");
+    int64_t m = count_lines(L);
+    if (m < 0) return fail(SP_EINVAL, "invalid line list (kind, counts or m)");
+    if (m > 0x7fffffffLL) return fail(SP_EUNSUPPORTED, "more than 2^31-1 lines");
+    switch (L->kind) {
+    case SP_LINES_THETA_Y:
+        if (m > 0 && (!L->theta || !L->y)) return fail(SP_EINVAL, "theta/y pointers are NULL");
+        break;
+    case SP_LINES_POINTS:
+        if (m > 0 && (!L->src || !L->dst)) return fail(SP_EINVAL, "src/dst pointers are NULL");
+        break;
+    case SP_LINES_PARALLEL:
+        if (!L->view) return fail(SP_EINVAL, "view angles pointer is NULL");
+        if (!finite(L->det0) || !finite(L->ddet)) return fail(SP_EINVAL, "det0/ddet must be finite");
+        break;
+    case SP_LINES_FAN:
+        if (!L->view) return fail(SP_EINVAL, "view angles pointer is NULL");
+        if (!finite(L->det0) || !finite(L->ddet)) return fail(SP_EINVAL, "det0/ddet must be finite");
+        if (!finite(L->dso) || !finite(L->dod) || !(L->dso > 0.f) || !((double)L->dso + L->dod > 0.0))
+            return fail(SP_EINVAL, "fan needs dso > 0 and dso + dod > 0");
+        break;
+    }
+    *out = spx::LinesDev{L->kind, L->n_view, L->n_det, m, L->theta, L->y, L->src, L->dst, L->view,
+                         L->det0, L->ddet, L->dso, L->dod};
+    return SP_OK;
+}
+
+int64_t table_count(const spx::LinesDev &L)
+{
+    return L.kind == SP_LINES_PARALLEL ? (int64_t)L.n_view : L.m;
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Line records and footprint tables for (grid, lines) in the workspace.
+sp_status prepare(const spx::GridDev &g, const spx::LinesDev &L, cudaStream_t s,
+                  spx::LineHdr **hdr, float **tabs)
+{
+    const int64_t nt = table_count(L);
+    size_t hb = align_up(sizeof(spx::LineHdr) * (size_t)L.m);
+    size_t tb = align_up(sizeof(float) * (size_t)spx::kTabFloats * (size_t)nt);
+    void *ws = nullptr;
+    sp_status st = workspace(hb + tb + 256, &ws);
+    if (st != SP_OK) return st;
+    *hdr = reinterpret_cast<spx::LineHdr *>(ws);
+    *tabs = reinterpret_cast<float *>(static_cast<char *>(ws) + hb);
+    cudaError_t e = spx::launch_setup(g, L, *hdr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "line setup");
+    e = spx::launch_tables(g, L, *tabs, nt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "footprint tables");
+    return SP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t sp_lines_count(const sp_lines *lines) { return count_lines(lines); }
+
+sp_status spline_project_fwd(const sp_grid *grid, const float *coef, const sp_lines *lines,
+                             float *sino, void *stream)
+{
+    g_err.clear();
+    spx::GridDev g;
+    spx::LinesDev L;
+    sp_status st = check_grid(grid, &g);
+    if (st != SP_OK) return st;
+    if ((st = check_lines(lines, &L)) != SP_OK) return st;
+    if (L.m == 0) return SP_OK;
+    if (!coef || !sino) return fail(SP_EINVAL, "coef/sino pointers are NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    spx::LineHdr *hdr;
+    float *tabs;
+    if ((st = prepare(g, L, s, &hdr, &tabs)) != SP_OK) return st;
+    cudaError_t e = spx::launch_fwd(g, hdr, tabs, L.m, coef, sino, s);
+    if (e != cudaSuccess) return cuda_fail(e, "forward projection");
+    return SP_OK;
+}
+
+sp_status spline_project_adj(const sp_grid *grid, const float *sino, const sp_lines *lines,
+                             float *coef_out, void *stream)
+{
+    g_err.clear();
+    spx::GridDev g;
+    spx::LinesDev L;
+    sp_status st = check_grid(grid, &g);
+    if (st != SP_OK) return st;
+    if ((st = check_lines(lines, &L)) != SP_OK) return st;
+    if (!coef_out) return fail(SP_EINVAL, "coef_out pointer is NULL");
+    if (L.m > 0 && !sino) return fail(SP_EINVAL, "sino pointer is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (L.m == 0) {
+        cudaError_t e = cudaMemsetAsync(coef_out, 0, sizeof(float) * (size_t)g.nx * g.ny, s);
+        return e == cudaSuccess ? SP_OK : cuda_fail(e, "cudaMemsetAsync");
+    }
+    spx::LineHdr *hdr;
+    float *tabs;
+    if ((st = prepare(g, L, s, &hdr, &tabs)) != SP_OK) return st;
+    cudaError_t e = spx::launch_adj(g, hdr, tabs, L.m, sino, coef_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint projection");
+    return SP_OK;
+}
+
+sp_status spline_lines_expand(const sp_lines *lines, float *theta_out, float *y_out, void *stream)
+{
+    g_err.clear();
+    spx::LinesDev L;
+    sp_status st = check_lines(lines, &L);
+    if (st != SP_OK) return st;
+    cudaError_t e = spx::launch_expand(L, theta_out, y_out, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SP_OK : cuda_fail(e, "line expansion");
+}
+
+sp_status spline_footprint_eval(int32_t degree, int64_t count, const float *theta, const float *yt,
+                                float *out, void *stream)
+{
+    g_err.clear();
+    if (degree < 0 || degree > 3) return fail(SP_EINVAL, "degree must be 0..3");
+    if (count < 0) return fail(SP_EINVAL, "count must be >= 0");
+    if (count == 0) return SP_OK;
+    if (!theta || !yt || !out) return fail(SP_EINVAL, "NULL pointer");
+    void *ws = nullptr;
+    sp_status st = workspace(sizeof(float) * (size_t)spx::kTabFloats * (size_t)count, &ws);
+    if (st != SP_OK) return st;
+    cudaError_t e = spx::launch_footprint_eval(degree, count, theta, yt, out, static_cast<float *>(ws),
+                                               static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SP_OK : cuda_fail(e, "footprint evaluation");
+}
+
+sp_status spline_visited(const sp_grid *grid, const sp_lines *lines, int32_t *counts,
+                         const int64_t *offsets, int32_t *nodes, void *stream)
+{
+    g_err.clear();
+    spx::GridDev g;
+    spx::LinesDev L;
+    sp_status st = check_grid(grid, &g);
+    if (st != SP_OK) return st;
+    if ((st = check_lines(lines, &L)) != SP_OK) return st;
+    if (L.m == 0) return SP_OK;
+    if (!counts) return fail(SP_EINVAL, "counts pointer is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    spx::LineHdr *hdr;
+    float *tabs;
+    if ((st = prepare(g, L, s, &hdr, &tabs)) != SP_OK) return st;
+    cudaError_t e = spx::launch_visited(g, hdr, tabs, L.m, counts, offsets, nodes, s);
+    return e == cudaSuccess ? SP_OK : cuda_fail(e, "visited set");
+}
+
+struct sp_plan {
+    spx::GridDev g;
+    spx::LinesDev L;
+    int device;
+    void *mem;
+    spx::LineHdr *hdr;
+    float *tabs;
+    bool prepared;
+};
+
+sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan **plan)
+{
+    g_err.clear();
+    if (!plan) return fail(SP_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    spx::GridDev g;
+    spx::LinesDev L;
+    sp_status st = check_grid(grid, &g);
+    if (st != SP_OK) return st;
+    if ((st = check_lines(lines, &L)) != SP_OK) return st;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    size_t hb = align_up(sizeof(spx::LineHdr) * (size_t)L.m);
+    size_t tb = align_up(sizeof(float) * (size_t)spx::kTabFloats * (size_t)table_count(L));
+    void *mem = nullptr;
+    if (hb + tb > 0) {
+        e = cudaMalloc(&mem, hb + tb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SP_ENOMEM, std::string("plan allocation failed: ") + cudaGetErrorString(e));
+        }
+    }
+    sp_plan *p = new sp_plan;
+    p->g = g;
+    p->L = L;
+    p->device = dev;
+    p->mem = mem;
+    p->hdr = reinterpret_cast<spx::LineHdr *>(mem);
+    p->tabs = mem ? reinterpret_cast<float *>(static_cast<char *>(mem) + hb) : nullptr;
+    p->prepared = false;
+    *plan = p;
+    return SP_OK;
+}
+
+sp_status spline_plan_prepare(sp_plan *plan, void *stream)
+{
+    g_err.clear();
+    if (!plan) return fail(SP_EINVAL, "plan is NULL");
+    if (plan->L.m == 0) { plan->prepared = true; return SP_OK; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = spx::launch_setup(plan->g, plan->L, plan->hdr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "line setup");
+    e = spx::launch_tables(plan->g, plan->L, plan->tabs, table_count(plan->L), s);
+    if (e != cudaSuccess) return cuda_fail(e, "footprint tables");
+    plan->prepared = true;
+    return SP_OK;
+}
+
+sp_status spline_plan_fwd(const sp_plan *plan, const float *coef, float *sino, void *stream)
+{
+    g_err.clear();
+    if (!plan) return fail(SP_EINVAL, "plan is NULL");
+    if (!plan->prepared) return fail(SP_EINVAL, "plan not prepared");
+    if (plan->L.m == 0) return SP_OK;
+    if (!coef || !sino) return fail(SP_EINVAL, "coef/sino pointers are NULL");
+    cudaError_t e = spx::launch_fwd(plan->g, plan->hdr, plan->tabs, plan->L.m, coef, sino,
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SP_OK : cuda_fail(e, "forward projection");
+}
+
+sp_status spline_plan_adj(const sp_plan *plan, const float *sino, float *coef_out, void *stream)
+{
+    g_err.clear();
+    if (!plan) return fail(SP_EINVAL, "plan is NULL");
+    if (!plan->prepared) return fail(SP_EINVAL, "plan not prepared");
+    if (!coef_out) return fail(SP_EINVAL, "coef_out pointer is NULL");
+    if (plan->L.m > 0 && !sino) return fail(SP_EINVAL, "sino pointer is NULL");
+    cudaError_t e = spx::launch_adj(plan->g, plan->hdr, plan->tabs, plan->L.m, sino, coef_out,
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SP_OK : cuda_fail(e, "adjoint projection");
+}
+
+int64_t spline_plan_lines(const sp_plan *plan) { return plan ? plan->L.m : -1; }
+
+sp_status spline_plan_destroy(sp_plan *plan)
+{
+    g_err.clear();
+    if (!plan) return SP_OK;
+    sp_status st = SP_OK;
+    if (plan->mem) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaDeviceSynchronize");
+        cudaFree(plan->mem);
+    }
+    delete plan;
+    return st;
+}
+
+sp_status sp_release_workspace(void)
+{
+    g_err.clear();
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return SP_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace &ws = g_ws[dev];
+    if (ws.ptr) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+        cudaFree(ws.ptr);
+    }
+    ws.ptr = nullptr;
+    ws.bytes = 0;
+    return SP_OK;
+}
+
+const char *sp_last_error(void) { return g_err.c_str(); }
+
+int32_t sp_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// Internal declarations shared by the CUDA translation units of the projector.
+//
+// Geometry of one line in grid units.  For node (i, j) the offset of the line
+// is y~ = (y - <x_k, theta^perp>)/h (Sec. IV.A), and u = y~ + w with
+// w = (n+1)(a+b)/2 the half-width of the support of phi_theta, a = max(|cos|,
+// |sin|), b = min(|cos|, |sin|) (Prop. 1 with D = 2).  A pair is nonzero iff
+// u is in (0, 2w).
+//
+// Rows follow the major axis of the line's direction (x2 for "mainly
+// vertical" lines, x1 otherwise, as in Algorithm 2) and columns the minor
+// axis, so that along a row u moves by +-a per column and by rho (|rho| = b)
+// per row.  In row r the nonzero columns form one run of at most K <= 2(n+1)
+// consecutive columns (Lemma 1 with K = n neighbours each side of the crossed
+// cells).  Writing u_0 in (0, a] for the smallest u of the run, candidate i of
+// the run sits at u_0 + i a.
+//
+// Footprint tables.  phi_theta is a piecewise polynomial of degree 2n+1 with
+// breakpoints p a + q b (p, q = 0..n+1) in u.  As a function of u_0, the
+// value at candidate i, phi(u_0 + i a), changes polynomial only where u_0
+// crosses one of the points s_q = (q b) mod a, so (0, a] splits into at most
+// n+2 intervals (s_sigma, s_{sigma+1}].  The table holds, for every interval
+// sigma and candidate i, the polynomial T[sigma][i](t) = phi(s_sigma + i a + t)
+// in t = u_0 - s_sigma: evaluating a pair is one Horner scheme of degree 2n+1.
+// It is built per line (per view for parallel beams) in FP32, stably:
+//   - derivatives n+1..2n+1 at each breakpoint directly from
+//     phi^{(n+1+e)}(u) = a^{-(n+1)} sum_p (-1)^p C(n+1,p) B^{(e)}(u - p a),
+//     B the B-spline of width (n+1) b (no cancellation);
+//   - derivatives 0..n carried from piece to piece by Taylor shifts whose
+//     lengths are formed from the integer breakpoint coordinates (p, q),
+//     walking only up to the centre of the support, the other half by the
+//     symmetry phi(u) = phi(2w - u).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/spline_project.h"
+
+namespace spx {
+
+constexpr int kMaxDeg = 3;
+constexpr int kMaxM = kMaxDeg + 1;            // n + 1
+constexpr int kMaxSig = kMaxM + 1;            // u_0 intervals
+constexpr int kMaxK = 2 * kMaxM;              // candidate slots per row
+constexpr int kNC = 2 * kMaxDeg + 2;          // coefficients of one polynomial
+constexpr int kSigStride = kMaxK * kNC;       // 64 floats
+constexpr int kTabHead = 8;                   // s_1..s_m padded to 8 floats
+constexpr int kTabFloats = kTabHead + kMaxSig * kSigStride;   // 328 floats
+constexpr float kBMin = 1e-7f;                // below this b is taken as 0 (Dirac)
+
+enum LineFlags : int {
+    kVert = 1,        // rows are x2 (index j), columns x1 (index i)
+    kKapNeg = 2,      // u decreases with the column index
+    kDeg0Axis = 4,    // degree 0 and b == 0: rectangle, midpoint value at its edges
+    kEmpty = 8,       // the line meets no support
+};
+
+// Per-line record (64 bytes).  u(r, q) = U0 + (r - r_ref) rho + (q - q_ref) kappa,
+// kappa = +-a; rho and a are carried as hi + lo pairs whose hi parts make the
+// products with row and step counts exact.
+struct __align__(16) LineHdr {
+    float U0;              // u at (r_ref, q_ref), in (0, a]
+    float rho_hi, rho_lo;  // u step per row
+    float a_hi, a_lo;      // a = a_hi + a_lo
+    float a;               // |kappa| as one float
+    float two_w;           // 2w
+    int r_ref, q_ref;
+    int r_begin, r_end;    // rows to visit, [r_begin, r_end)
+    int flags;
+    int tab;               // index of the footprint table
+    int K;                 // candidate slots per row
+    float pad[2];
+};
+static_assert(sizeof(LineHdr) == 64, "LineHdr layout");
+
+struct GridDev {
+    int nx, ny, degree;
+    float h, cx, cy;
+};
+
+struct LinesDev {
+    int kind, n_view, n_det;
+    int64_t m;
+    const float *theta, *y, *src, *dst, *view;
+    float det0, ddet, dso, dod;
+};
+
+// Exactly-rounded u_0 of row r for a given step count k:
+// u_0 = U0 + dr*rho - k*a, with the hi products exact.
+__device__ __forceinline__ float row_u0(const LineHdr &H, int dr, int k)
+{
+    float fr = (float)dr, fk = (float)k;
+    float big = __fsub_rn(__fmul_rn(fr, H.rho_hi), __fmul_rn(fk, H.a_hi));
+    float small = __fmaf_rn(fr, H.rho_lo, __fmul_rn(-fk, H.a_lo));
+    return __fadd_rn(__fadd_rn(H.U0, small), big);
+}
+
+// Row setup: the step count k and u_0 in (0, a] of row r.
+__device__ __forceinline__ float row_start(const LineHdr &H, float inv_a, int r, int &k)
+{
+    int dr = r - H.r_ref;
+    float V = __fmaf_rn((float)dr, H.rho_hi + H.rho_lo, H.U0);
+    k = (int)ceilf(V * inv_a) - 1;
+    float u0 = row_u0(H, dr, k);
+    if (u0 <= 0.0f) { k -= 1; u0 = row_u0(H, dr, k); }
+    else if (u0 > H.a) { k += 1; u0 = row_u0(H, dr, k); }
+    return u0;
+}
+
+// Kernel launchers (kernels.cu).
+cudaError_t launch_setup(const GridDev &g, const LinesDev &L, LineHdr *hdr, cudaStream_t s);
+cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int64_t n_tab,
+                          cudaStream_t s);
+cudaError_t launch_fwd(const GridDev &g, const LineHdr *hdr, const float *tabs, int64_t m,
+                       const float *coef, float *sino, cudaStream_t s);
+cudaError_t launch_adj(const GridDev &g, const LineHdr *hdr, const float *tabs, int64_t m,
+                       const float *sino, float *coef_out, cudaStream_t s);
+cudaError_t launch_visited(const GridDev &g, const LineHdr *hdr, const float *tabs, int64_t m,
+                           int32_t *counts, const int64_t *offsets, int32_t *nodes,
+                           cudaStream_t s);
+cudaError_t launch_expand(const LinesDev &L, float *theta_out, float *y_out, cudaStream_t s);
+cudaError_t launch_footprint_eval(int degree, int64_t count, const float *theta, const float *yt,
+                                  float *out, float *scratch, cudaStream_t s);
+
+}  // namespace spx

@@ -1,0 +1,676 @@
+// Kernels of the spline x-ray projector: line setup, footprint tables,
+// forward projection, adjoint, visited-set listing, line expansion and a
+// footprint probe.  The method is that of "Generalized Ray Tracing with Basis
+// Functions for Tomographic Projections" (arXiv 2503.20907); see common.cuh
+// for the geometry and the table layout.
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace spx {
+namespace {
+
+// Left-anchored B-spline beta^n on [0, n+1] (Sec. III.C, centred beta^n
+// shifted by (n+1)/2), piece l on x = l + tau, tau in [0, 1): coefficients of
+// tau^0..tau^n, from beta^n(x) = 1/n! sum_k (-1)^k C(n+1,k) (x-k)_+^n.
+__constant__ float kBPiece[4][4][4] = {
+    {{1.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}},
+    {{0.f, 1.f, 0.f, 0.f}, {1.f, -1.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}},
+    {{0.f, 0.f, 0.5f, 0.f}, {0.5f, 1.f, -1.f, 0.f}, {0.5f, -1.f, 0.5f, 0.f}, {0.f, 0.f, 0.f, 0.f}},
+    {{0.f, 0.f, 0.f, 1.f / 6.f}, {1.f / 6.f, 0.5f, 0.5f, -0.5f}, {2.f / 3.f, 0.f, -1.f, 0.5f},
+     {1.f / 6.f, -0.5f, 0.5f, -1.f / 6.f}},
+};
+
+__device__ __forceinline__ float binomf(int n, int k)
+{
+    float r = 1.f;
+    for (int i = 1; i <= k; ++i) r = r * (float)(n - k + i) / (float)i;
+    return r;
+}
+
+__device__ __forceinline__ float factf(int n)
+{
+    float r = 1.f;
+    for (int i = 2; i <= n; ++i) r *= (float)i;
+    return r;
+}
+
+// Unit direction (dx, dy) and a point (px, py) of line r, in double.
+__device__ void line_geometry(const LinesDev &L, int64_t r, double &dx, double &dy, double &px,
+                              double &py)
+{
+    switch (L.kind) {
+    case SP_LINES_THETA_Y: {
+        double th = (double)L.theta[r], yy = (double)L.y[r], s, c;
+        sincos(th, &s, &c);
+        dx = c; dy = s; px = yy * s; py = -yy * c;
+        break;
+    }
+    case SP_LINES_POINTS: {
+        double sx = L.src[2 * r], sy = L.src[2 * r + 1];
+        double vx = (double)L.dst[2 * r] - sx, vy = (double)L.dst[2 * r + 1] - sy;
+        double inv = 1.0 / sqrt(vx * vx + vy * vy);
+        dx = vx * inv; dy = vy * inv; px = sx; py = sy;
+        break;
+    }
+    case SP_LINES_PARALLEL: {
+        int64_t v = r / L.n_det, j = r - v * L.n_det;
+        double th = (double)L.view[v], s, c;
+        sincos(th, &s, &c);
+        double yy = (double)L.det0 + (double)j * (double)L.ddet;
+        dx = c; dy = s; px = yy * s; py = -yy * c;
+        break;
+    }
+    default: {  // SP_LINES_FAN
+        int64_t v = r / L.n_det, j = r - v * L.n_det;
+        double be = (double)L.view[v], sb, cb;
+        sincos(be, &sb, &cb);
+        double sx = (double)L.dso * cb, sy = (double)L.dso * sb;
+        double off = (double)L.det0 + (double)j * (double)L.ddet;
+        double ex = -(double)L.dod * cb - off * sb, ey = -(double)L.dod * sb + off * cb;
+        double vx = ex - sx, vy = ey - sy;
+        double inv = 1.0 / sqrt(vx * vx + vy * vy);
+        dx = vx * inv; dy = vy * inv; px = sx; py = sy;
+        break;
+    }
+    }
+}
+
+// The footprint parameters a, b as the table uses them.
+__device__ __forceinline__ void footprint_ab(double dx, double dy, float &af, float &bf)
+{
+    af = (float)fmax(fabs(dx), fabs(dy));
+    bf = (float)fmin(fabs(dx), fabs(dy));
+    if (bf < kBMin) bf = 0.f;
+}
+
+__device__ __forceinline__ float two_w_of(int m, float af, float bf)
+{
+    return (float)((double)m * ((double)af + (double)bf));
+}
+
+__device__ __forceinline__ int slots_of(int m, float af, float bf, float two_w)
+{
+    if (bf == 0.f) return m;
+    int K = (int)floorf(two_w / af) + 1;
+    return K < 2 * m ? K : 2 * m;
+}
+
+// Split x into hi + lo with hi carrying `bits` significant bits.
+__device__ void split_hi_lo(double x, int bits, float &hi, float &lo)
+{
+    if (x == 0.0) { hi = 0.f; lo = 0.f; return; }
+    int e;
+    frexp(x, &e);
+    double sc = ldexp(1.0, bits - e);
+    double xh = rint(x * sc) / sc;
+    hi = (float)xh;
+    lo = (float)(x - xh);
+}
+
+// ------------------------------------------------------------------ setup
+__global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, int64_t M)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    double dx, dy, px, py;
+    line_geometry(L, r, dx, dy, px, py);
+    const int m = g.degree + 1;
+    LineHdr H;
+    H.pad[0] = H.pad[1] = 0.f;
+    H.tab = (L.kind == SP_LINES_PARALLEL) ? (int)(r / L.n_det) : (int)r;
+    float af, bf;
+    footprint_ab(dx, dy, af, bf);
+    H.two_w = two_w_of(m, af, bf);
+    H.K = slots_of(m, af, bf, H.two_w);
+    const bool vert = fabs(dy) >= fabs(dx);
+    const double A = fmax(fabs(dx), fabs(dy));
+    const double B = fmin(fabs(dx), fabs(dy));
+    const double h = (double)g.h;
+    const double Yhat = ((px - (double)g.cx) * dy - (py - (double)g.cy) * dx) / h;
+    const double ic = 0.5 * (g.nx - 1), jc = 0.5 * (g.ny - 1);
+    double kap, rho, rc, qc;
+    int Nr, Nq;
+    if (vert) { kap = -dy; rho = dx; rc = jc; qc = ic; Nr = g.ny; Nq = g.nx; }
+    else { kap = dx; rho = -dy; rc = ic; qc = jc; Nr = g.nx; Nq = g.ny; }
+    const int sgn = kap > 0.0 ? 1 : -1;
+    const double w = 0.5 * (double)H.two_w;
+    int flags = (vert ? kVert : 0) | (sgn < 0 ? kKapNeg : 0);
+    if (g.degree == 0 && B == 0.0) flags |= kDeg0Axis;
+
+    // Rows whose support run meets the columns [0, Nq): the column of the
+    // support centre (u = w) moves linearly with the row.
+    const double lo = -w / A - 2.0, hi = (double)(Nq - 1) + w / A + 2.0;
+    const double c0 = qc - (Yhat - rc * rho) / kap;   // centre column at row 0
+    const double gam = -rho / kap;
+    int rb = 0, re = 0;
+    if (fabs(gam) < 1e-300) {
+        if (c0 >= lo && c0 <= hi) { rb = 0; re = Nr; }
+    } else {
+        double t0 = (lo - c0) / gam, t1 = (hi - c0) / gam;
+        if (t0 > t1) { double t = t0; t0 = t1; t1 = t; }
+        t0 = fmax(floor(t0) - 1.0, 0.0);
+        t1 = fmin(ceil(t1) + 2.0, (double)Nr);
+        if (t1 > t0) { rb = (int)t0; re = (int)t1; }
+    }
+    if (rb >= re || !(Yhat == Yhat)) {
+        H.flags = flags | kEmpty;
+        H.U0 = H.rho_hi = H.rho_lo = H.a_hi = H.a_lo = 0.f;
+        H.a = af;
+        H.r_ref = H.q_ref = H.r_begin = H.r_end = 0;
+        hdr[r] = H;
+        return;
+    }
+    const int r_ref = (rb + re) / 2;
+    // u at (r_ref, q = 0), then the reference column with U0 in (0, a].
+    const double Ur = Yhat + w + ((double)r_ref - rc) * rho - qc * kap;
+    double qr = (sgn > 0) ? floor(-Ur / A) + 1.0 : ceil(Ur / A) - 1.0;
+    double U0 = Ur + qr * kap;
+    if (U0 <= 0.0) { qr += sgn; U0 = Ur + qr * kap; }
+    else if (U0 > A) { qr -= sgn; U0 = Ur + qr * kap; }
+    // hi parts exact against |row offset| and |step count|, both < maxc
+    int maxc = (re - rb) + 8;
+    int nb = 0;
+    while ((1 << nb) <= maxc) ++nb;
+    const int bits = 23 - nb;
+    H.U0 = (float)U0;
+    split_hi_lo(rho, bits, H.rho_hi, H.rho_lo);
+    split_hi_lo(A, bits, H.a_hi, H.a_lo);
+    H.a = (float)A;
+    H.r_ref = r_ref;
+    H.q_ref = (int)qr;
+    H.r_begin = rb;
+    H.r_end = re;
+    H.flags = flags;
+    hdr[r] = H;
+}
+
+// ------------------------------------------------------------------ tables
+// Derivatives e = 0..n of B-spline piece l at tau, times b^-(1+e).
+__device__ __forceinline__ void bspline_piece_derivs(int n, int l, float tau, float binv, float *D)
+{
+    float sc = binv;
+    for (int e = 0; e <= n; ++e) {
+        float acc = 0.f;
+        for (int k = n; k >= e; --k) {
+            float ff = 1.f;   // k!/(k-e)!
+            for (int t = 0; t < e; ++t) ff *= (float)(k - t);
+            acc = acc * tau + kBPiece[n][l][k] * ff;
+        }
+        D[e] = acc * sc;
+        sc *= binv;
+    }
+}
+
+// Sign of (pa + qb) - (p2 a + q2 b) + extra, formed from the integer
+// differences so that it is accurate whatever the size of a and b.
+__device__ __forceinline__ float sym_diff(int dp, int dq, float a, float b, float extra)
+{
+    return __fmaf_rn((float)dp, a, __fmaf_rn((float)dq, b, extra));
+}
+
+// Build the footprint table of one direction (see common.cuh).
+__device__ void build_table(int n, float a, float b, float *out)
+{
+    const int m = n + 1;
+    const int nc = 2 * n + 2;
+    for (int k = 0; k < kTabFloats; ++k) out[k] = 0.f;
+    const float two_w = two_w_of(m, a, b);
+    const float ainv = 1.0f / a;
+    if (b == 0.f) {
+        // Dirac factor (Prop. 1): phi(u) = beta^n(u/a)/a on the a-knots.
+        for (int q = 0; q < kTabHead; ++q) out[q] = (q < m) ? a : FLT_MAX;
+        for (int i = 0; i < m; ++i) {
+            float sc = ainv;
+            for (int e = 0; e <= n; ++e) {
+                out[kTabHead + i * kNC + e] = kBPiece[n][i][e] * sc;
+                sc *= ainv;
+            }
+        }
+        return;
+    }
+    // breakpoints p a + q b, sorted (ties by p, then q)
+    float bv[25];
+    signed char bpp[25], bpq[25];
+    int nbp = 0;
+    for (int p = 0; p <= m; ++p)
+        for (int q = 0; q <= m; ++q) {
+            float v = __fmaf_rn((float)p, a, (float)q * b);
+            int t = nbp++;
+            while (t > 0 && (bv[t - 1] > v || (bv[t - 1] == v && (bpp[t - 1] > p ||
+                                                                 (bpp[t - 1] == p && bpq[t - 1] > q))))) {
+                bv[t] = bv[t - 1]; bpp[t] = bpp[t - 1]; bpq[t] = bpq[t - 1];
+                --t;
+            }
+            bv[t] = v; bpp[t] = (signed char)p; bpq[t] = (signed char)q;
+        }
+    // pieces that start at or before the centre w
+    int nh = 0;
+    while (nh < nbp && sym_diff(2 * bpp[nh] - m, 2 * bpq[nh] - m, a, b, 0.f) <= 0.f) ++nh;
+    if (nh < 1) nh = 1;
+
+    float P[25][8];
+    const float binv = 1.0f / b;
+    float am = 1.f;
+    for (int k = 0; k < m; ++k) am *= ainv;
+    for (int pi = 0; pi < nh; ++pi) {
+        const int p0 = bpp[pi], q0 = bpq[pi];
+        // derivatives n+1..2n+1 directly (right-sided at the breakpoint)
+        float hi[kMaxM];
+        for (int e = 0; e <= n; ++e) hi[e] = 0.f;
+        for (int pp = 0; pp <= m; ++pp) {
+            int l;
+            float tau;
+            if (pp == p0) {
+                if (q0 >= m) continue;
+                l = q0; tau = 0.f;
+            } else {
+                float v = __fmaf_rn((float)(p0 - pp), a, (float)q0 * b);
+                if (v < 0.f) continue;
+                float t = v * binv;
+                l = (int)floorf(t);
+                if (l < 0 || l >= m) continue;
+                tau = t - (float)l;
+            }
+            float D[kMaxM];
+            bspline_piece_derivs(n, l, tau, binv, D);
+            float wp = binomf(m, pp) * ((pp & 1) ? -1.f : 1.f);
+            for (int e = 0; e <= n; ++e) hi[e] = __fmaf_rn(wp, D[e], hi[e]);
+        }
+        for (int e = 0; e <= n; ++e) P[pi][n + 1 + e] = hi[e] * am / factf(n + 1 + e);
+        // derivatives 0..n carried from the previous piece
+        if (pi == 0) {
+            for (int d = 0; d <= n; ++d) P[0][d] = 0.f;
+        } else {
+            float dl = sym_diff(p0 - bpp[pi - 1], q0 - bpq[pi - 1], a, b, 0.f);
+            for (int d = 0; d <= n; ++d) {
+                float s = 0.f;
+                for (int k = nc - 1; k >= d; --k) s = __fmaf_rn(s, dl, binomf(k, d) * P[pi - 1][k]);
+                P[pi][d] = s;
+            }
+        }
+    }
+    // u_0 interval ends s_q = (q b) mod a in (0, a], sorted
+    float sv[kMaxSig];
+    int sq[kMaxSig], sf[kMaxSig];
+    sv[0] = 0.f; sq[0] = 0; sf[0] = 0;
+    for (int q = 1; q <= m; ++q) {
+        int f = (int)floorf((float)q * b * ainv);
+        float r = __fmaf_rn((float)(-f), a, (float)q * b);
+        if (r <= 0.f) { f -= 1; r = __fmaf_rn((float)(-f), a, (float)q * b); }
+        else if (r > a) { f += 1; r = __fmaf_rn((float)(-f), a, (float)q * b); }
+        int t = q;
+        while (t > 1 && sv[t - 1] > r) { sv[t] = sv[t - 1]; sq[t] = sq[t - 1]; sf[t] = sf[t - 1]; --t; }
+        sv[t] = r; sq[t] = q; sf[t] = f;
+    }
+    for (int q = 0; q < kTabHead; ++q) out[q] = (q < m) ? sv[q + 1] : FLT_MAX;
+    const int K = slots_of(m, a, b, two_w);
+    for (int sg = 0; sg <= m; ++sg) {
+        const float hw = 0.5f * (((sg < m) ? sv[sg + 1] : a) - sv[sg]);
+        for (int i = 0; i < K; ++i) {
+            // interval start u_lo = (i - f) a + q b; midpoint u_lo + hw
+            const int pl = i - sf[sg], ql = sq[sg];
+            if (sym_diff(pl - m, ql - m, a, b, hw) >= 0.f) continue;          // beyond 2w
+            const bool mirror = sym_diff(2 * pl - m, 2 * ql - m, a, b, 2.f * hw) > 0.f;
+            int pi = 0;
+            if (!mirror) {
+                while (pi + 1 < nh && sym_diff(pl - bpp[pi + 1], ql - bpq[pi + 1], a, b, hw) >= 0.f) ++pi;
+            } else {
+                while (pi + 1 < nh && sym_diff(m - pl - bpp[pi + 1], m - ql - bpq[pi + 1], a, b, -hw) >= 0.f) ++pi;
+            }
+            float X = mirror ? sym_diff(m - pl - bpp[pi], m - ql - bpq[pi], a, b, 0.f)
+                             : sym_diff(pl - bpp[pi], ql - bpq[pi], a, b, 0.f);
+            float *T = out + kTabHead + sg * kSigStride + i * kNC;
+            for (int d = 0; d < nc; ++d) {
+                float s = 0.f;
+                for (int k = nc - 1; k >= d; --k) s = __fmaf_rn(s, X, binomf(k, d) * P[pi][k]);
+                T[d] = (mirror && (d & 1)) ? -s : s;
+            }
+        }
+    }
+}
+
+__global__ void tables_kernel(GridDev g, LinesDev L, float *tabs, int64_t n_tab)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tab) return;
+    double dx, dy;
+    if (L.kind == SP_LINES_PARALLEL) {
+        double s, c;
+        sincos((double)L.view[t], &s, &c);
+        dx = c; dy = s;
+    } else {
+        double px, py;
+        line_geometry(L, t, dx, dy, px, py);
+    }
+    float af, bf;
+    footprint_ab(dx, dy, af, bf);
+    build_table(g.degree, af, bf, tabs + t * (int64_t)kTabFloats);
+}
+
+// ------------------------------------------------------------------ evaluation
+template <int DEG>
+__device__ __forceinline__ float horner(const float *T, float t)
+{
+    constexpr int NC = 2 * DEG + 2;
+    float s = T[NC - 1];
+#pragma unroll
+    for (int d = NC - 2; d >= 0; --d) s = __fmaf_rn(s, t, T[d]);
+    return s;
+}
+
+template <int DEG>
+__device__ __forceinline__ int sigma_of(const float *s, float u0, float &s_lo)
+{
+    int sg = 0;
+    s_lo = 0.f;
+#pragma unroll
+    for (int q = 0; q <= DEG; ++q) {
+        float v = s[q];
+        if (v < u0) { sg = q + 1; s_lo = v; }
+    }
+    return sg;
+}
+
+struct RowCtx {
+    int k, q0, sgn;
+    float u0, t;
+    const float *T;   // table row of the interval
+};
+
+// Visit every candidate of every row of one line; `op(node, phi)` is called
+// for in-grid candidates (phi may be 0 beyond the support).
+template <int DEG, typename Op>
+__device__ __forceinline__ void walk_line(const LineHdr &H, const float *tab, const GridDev &g,
+                                          int lane, Op op)
+{
+    const bool vert = H.flags & kVert;
+    const int sgn = (H.flags & kKapNeg) ? -1 : 1;
+    const int Nq = vert ? g.nx : g.ny;
+    const float inv_a = 1.0f / H.a;
+    float s[DEG + 1];
+#pragma unroll
+    for (int q = 0; q <= DEG; ++q) s[q] = tab[q];
+    for (int r = H.r_begin + lane; r < H.r_end; r += 32) {
+        int k;
+        float u0 = row_start(H, inv_a, r, k);
+        float s_lo;
+        int sg = sigma_of<DEG>(s, u0, s_lo);
+        float t = u0 - s_lo;
+        const float *T = tab + kTabHead + sg * kSigStride;
+        int q0 = H.q_ref - sgn * k;
+        for (int i = 0; i < H.K; ++i) {
+            int q = q0 + sgn * i;
+            if ((unsigned)q < (unsigned)Nq) {
+                float phi = horner<DEG>(T + i * kNC, t);
+                if (DEG == 0 && (H.flags & kDeg0Axis) && u0 == H.a) phi = 0.5f * phi;
+                int node = vert ? r * g.nx + q : q * g.nx + r;
+                op(node, phi);
+            }
+        }
+        if (DEG == 0 && (H.flags & kDeg0Axis) && u0 == H.a) {
+            // the run also starts at u = 0: midpoint value on that edge too
+            int q = q0 - sgn;
+            if ((unsigned)q < (unsigned)Nq) {
+                int node = vert ? r * g.nx + q : q * g.nx + r;
+                op(node, 0.5f * inv_a);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) fwd_kernel(GridDev g, const LineHdr *__restrict__ hdr,
+                                                  const float *__restrict__ tabs, int64_t M,
+                                                  const float *__restrict__ coef,
+                                                  float *__restrict__ sino)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); line < M;
+         line += nw) {
+        const LineHdr H = hdr[line];
+        float acc = 0.f;
+        if (!(H.flags & kEmpty)) {
+            const float *tab = tabs + (int64_t)H.tab * kTabFloats;
+            walk_line<DEG>(H, tab, g, lane, [&](int node, float phi) {
+                acc = __fmaf_rn(__ldg(coef + node), phi, acc);
+            });
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) sino[line] = g.h * acc;
+    }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) adj_kernel(GridDev g, const LineHdr *__restrict__ hdr,
+                                                  const float *__restrict__ tabs, int64_t M,
+                                                  const float *__restrict__ sino,
+                                                  float *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); line < M;
+         line += nw) {
+        const LineHdr H = hdr[line];
+        if (H.flags & kEmpty) continue;
+        const float hp = g.h * __ldg(sino + line);
+        if (hp == 0.f) continue;
+        const float *tab = tabs + (int64_t)H.tab * kTabFloats;
+        walk_line<DEG>(H, tab, g, lane, [&](int node, float phi) {
+            atomicAdd(out + node, hp * phi);
+        });
+    }
+}
+
+template <int DEG>
+__global__ void visited_kernel(GridDev g, const LineHdr *__restrict__ hdr,
+                               const float *__restrict__ tabs, int64_t M, int32_t *counts,
+                               const int64_t *offsets, int32_t *nodes)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); line < M;
+         line += nw) {
+        const LineHdr H = hdr[line];
+        int total = 0;
+        if (!(H.flags & kEmpty)) {
+            const bool vert = H.flags & kVert;
+            const int sgn = (H.flags & kKapNeg) ? -1 : 1;
+            const int Nq = vert ? g.nx : g.ny;
+            const float inv_a = 1.0f / H.a;
+            const bool ties = (DEG == 0) && (H.flags & kDeg0Axis);
+            int64_t base = offsets ? offsets[line] : 0;
+            // rows in rounds of 32 so that every lane's writes have a place
+            for (int r0 = H.r_begin; r0 < H.r_end; r0 += 32) {
+                int r = r0 + lane;
+                int cnt = 0, k = 0, q0 = 0;
+                float u0 = 0.f;
+                bool tie = false;
+                if (r < H.r_end) {
+                    u0 = row_start(H, inv_a, r, k);
+                    q0 = H.q_ref - sgn * k;
+                    tie = ties && u0 == H.a;
+                    for (int i = 0; i < H.K; ++i) {
+                        int q = q0 + sgn * i;
+                        float u = __fmaf_rn((float)i, H.a, u0);
+                        bool in = ties ? (u <= H.two_w) : (u < H.two_w);
+                        if ((unsigned)q < (unsigned)Nq && in) ++cnt;
+                    }
+                    if (tie && (unsigned)(q0 - sgn) < (unsigned)Nq) ++cnt;
+                }
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                int excl = incl - cnt;
+                int round_total = __shfl_sync(0xffffffffu, incl, 31);
+                if (nodes && offsets && cnt > 0) {
+                    int64_t pos = base + total + excl;
+                    for (int i = 0; i < H.K; ++i) {
+                        int q = q0 + sgn * i;
+                        float u = __fmaf_rn((float)i, H.a, u0);
+                        bool in = ties ? (u <= H.two_w) : (u < H.two_w);
+                        if ((unsigned)q < (unsigned)Nq && in)
+                            nodes[pos++] = vert ? r * g.nx + q : q * g.nx + r;
+                    }
+                    if (tie && (unsigned)(q0 - sgn) < (unsigned)Nq) {
+                        int q = q0 - sgn;
+                        nodes[pos++] = vert ? r * g.nx + q : q * g.nx + r;
+                    }
+                }
+                total += round_total;
+            }
+        }
+        if (lane == 0) counts[line] = total;
+    }
+}
+
+__global__ void expand_kernel(LinesDev L, int64_t M, float *theta_out, float *y_out)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    if (L.kind == SP_LINES_THETA_Y) {
+        if (theta_out) theta_out[r] = L.theta[r];
+        if (y_out) y_out[r] = L.y[r];
+        return;
+    }
+    double dx, dy, px, py;
+    line_geometry(L, r, dx, dy, px, py);
+    if (theta_out) theta_out[r] = (float)atan2(dy, dx);
+    if (y_out) y_out[r] = (float)(px * dy - py * dx);
+}
+
+template <int DEG>
+__device__ float footprint_from_table(const float *tab, float a, float b, float yt)
+{
+    const int m = DEG + 1;
+    const float two_w = two_w_of(m, a, b);
+    const float u = yt + 0.5f * two_w;
+    const bool ties = (DEG == 0) && (b == 0.f);
+    if (ties) {
+        if (u < 0.f || u > two_w) return 0.f;
+        if (u == 0.f || u == two_w) return 0.5f / a;
+    } else if (u <= 0.f || u >= two_w) {
+        return 0.f;
+    }
+    int i = (int)ceilf(u / a) - 1;
+    if (i < 0) i = 0;
+    float u0 = __fmaf_rn(-(float)i, a, u);
+    if (u0 <= 0.f) { i -= 1; u0 = __fmaf_rn(-(float)i, a, u); }
+    else if (u0 > a) { i += 1; u0 = __fmaf_rn(-(float)i, a, u); }
+    const int K = slots_of(m, a, b, two_w);
+    if (i < 0 || i >= K) return 0.f;
+    float s_lo;
+    int sg = sigma_of<DEG>(tab, u0, s_lo);
+    return horner<DEG>(tab + kTabHead + sg * kSigStride + i * kNC, u0 - s_lo);
+}
+
+template <int DEG>
+__global__ void footprint_eval_kernel(int64_t count, const float *theta, const float *yt,
+                                      float *out, float *scratch)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= count) return;
+    double s, c;
+    sincos((double)theta[r], &s, &c);
+    float af, bf;
+    footprint_ab(c, s, af, bf);
+    float *tab = scratch + r * (int64_t)kTabFloats;
+    build_table(DEG, af, bf, tab);
+    out[r] = footprint_from_table<DEG>(tab, af, bf, yt[r]);
+}
+
+inline unsigned blocks_for(int64_t n, int per)
+{
+    int64_t b = (n + per - 1) / per;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+inline unsigned warp_blocks(int64_t lines)
+{
+    // 8 warps per block, grid-stride; enough blocks for several waves on 152 SMs
+    int64_t b = (lines + 7) / 8;
+    if (b > 152 * 64) b = 152 * 64;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_setup(const GridDev &g, const LinesDev &L, LineHdr *hdr, cudaStream_t s)
+{
+    if (L.m <= 0) return cudaSuccess;
+    setup_kernel<<<blocks_for(L.m, 128), 128, 0, s>>>(g, L, hdr, L.m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int64_t n_tab,
+                          cudaStream_t s)
+{
+    if (n_tab <= 0) return cudaSuccess;
+    tables_kernel<<<blocks_for(n_tab, 64), 64, 0, s>>>(g, L, tabs, n_tab);
+    return cudaGetLastError();
+}
+
+#define SPX_DISPATCH(DEGVAR, KERNEL, GRID, BLOCK, STREAM, ...)                          \
+    switch (DEGVAR) {                                                                     \
+    case 0: KERNEL<0><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                    \
+    case 1: KERNEL<1><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                    \
+    case 2: KERNEL<2><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                    \
+    default: KERNEL<3><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                   \
+    }
+
+cudaError_t launch_fwd(const GridDev &g, const LineHdr *hdr, const float *tabs, int64_t m,
+                       const float *coef, float *sino, cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    SPX_DISPATCH(g.degree, fwd_kernel, warp_blocks(m), 256, s, g, hdr, tabs, m, coef, sino);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj(const GridDev &g, const LineHdr *hdr, const float *tabs, int64_t m,
+                       const float *sino, float *coef_out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(coef_out, 0, sizeof(float) * (size_t)g.nx * (size_t)g.ny, s);
+    if (e != cudaSuccess || m <= 0) return e;
+    SPX_DISPATCH(g.degree, adj_kernel, warp_blocks(m), 256, s, g, hdr, tabs, m, sino, coef_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_visited(const GridDev &g, const LineHdr *hdr, const float *tabs, int64_t m,
+                           int32_t *counts, const int64_t *offsets, int32_t *nodes,
+                           cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    SPX_DISPATCH(g.degree, visited_kernel, warp_blocks(m), 256, s, g, hdr, tabs, m, counts,
+                 offsets, nodes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const LinesDev &L, float *theta_out, float *y_out, cudaStream_t s)
+{
+    if (L.m <= 0) return cudaSuccess;
+    expand_kernel<<<blocks_for(L.m, 256), 256, 0, s>>>(L, L.m, theta_out, y_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_footprint_eval(int degree, int64_t count, const float *theta, const float *yt,
+                                  float *out, float *scratch, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    SPX_DISPATCH(degree, footprint_eval_kernel, blocks_for(count, 64), 64, s, count, theta, yt,
+                 out, scratch);
+    return cudaGetLastError();
+}
+
+}  // namespace spx

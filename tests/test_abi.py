@@ -1,0 +1,69 @@
+"""The C ABI without a GPU: the library builds, loads, exports every function
+that include/*.h declares, and rejects bad arguments on the host before any
+CUDA call."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_functions():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    sp = pytest.importorskip("paper_2503_20907_gb300")
+    return sp.load()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for n in ("spline_project_fwd", "spline_project_adj", "spline_lines_expand", "spline_visited",
+              "spline_footprint_eval", "sp_last_error", "sp_release_workspace", "sp_lines_count"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_host_side_argument_checks(lib):
+    from paper_2503_20907_gb300 import _lib as L
+    g = L.SpGrid(8, 8, 7, 0, 1.0, 0.0, 0.0)           # degree out of range
+    lines = L.SpLines()
+    lines.kind = L.KIND_THETA_Y
+    lines.m = 4
+    lines.theta = 1
+    lines.y = 1
+    st = lib.spline_project_fwd(ctypes.byref(g), 1, ctypes.byref(lines), 1, None)
+    assert st == L.SP_EINVAL
+    assert b"degree" in lib.sp_last_error()
+    g = L.SpGrid(8, 8, 3, 0, -1.0, 0.0, 0.0)          # negative spacing
+    assert lib.spline_project_adj(ctypes.byref(g), 1, ctypes.byref(lines), 1, None) == L.SP_EINVAL
+    g = L.SpGrid(8, 8, 3, 0, 1.0, 0.0, 0.0)
+    bad = L.SpLines()
+    bad.kind = 7                                       # unknown kind
+    assert lib.spline_project_fwd(ctypes.byref(g), 1, ctypes.byref(bad), 1, None) == L.SP_EINVAL
+    assert lib.sp_lines_count(ctypes.byref(bad)) == -1
+    fan = L.SpLines()
+    fan.kind = L.KIND_FAN
+    fan.n_view, fan.n_det, fan.view = 3, 5, 1
+    fan.dso, fan.dod, fan.ddet = -1.0, 1.0, 1.0        # source distance must be > 0
+    assert lib.spline_project_fwd(ctypes.byref(g), 1, ctypes.byref(fan), 1, None) == L.SP_EINVAL
+    fan.dso = 10.0
+    assert lib.sp_lines_count(ctypes.byref(fan)) == 15
+    fan.m = 14                                         # inconsistent count
+    assert lib.sp_lines_count(ctypes.byref(fan)) == -1
+    assert lib.spline_footprint_eval(9, 3, 1, 1, 1, None) == L.SP_EINVAL
+    assert lib.sp_version() >= 100
