@@ -44,7 +44,9 @@ constexpr int kMaxSig = kMaxM + 1;            // u_0 intervals
 constexpr int kMaxK = 2 * kMaxM;              // candidate slots per row
 constexpr int kNC = 2 * kMaxDeg + 2;          // coefficients of one polynomial
 constexpr int kSigStride = kMaxK * kNC;       // 64 floats
-constexpr int kTabHead = 8;                   // s_1..s_m padded to 8 floats
+constexpr int kTabHead = 8;                   // s_1..s_m (padded with FLT_MAX), a, b
+constexpr int kTabA = 6;                      // head slot of the a the table was built with
+constexpr int kTabB = 7;                      // head slot of its b
 constexpr int kTabFloats = kTabHead + kMaxSig * kSigStride;   // 328 floats
 constexpr float kBMin = 1e-7f;                // below this b is taken as 0 (Dirac)
 
@@ -69,7 +71,8 @@ struct __align__(16) LineHdr {
     int flags;
     int tab;               // index of the footprint table
     int K;                 // candidate slots per row
-    float pad[2];
+    float U0_lo;           // U0 = U0 (above) + U0_lo exactly enough for degree 0
+    float a_corr;          // |kappa| minus the a the footprint table was built with
 };
 static_assert(sizeof(LineHdr) == 64, "LineHdr layout");
 
@@ -105,6 +108,45 @@ __device__ __forceinline__ float row_start(const LineHdr &H, float inv_a, int r,
     if (u0 <= 0.0f) { k -= 1; u0 = row_u0(H, dr, k); }
     else if (u0 > H.a) { k += 1; u0 = row_u0(H, dr, k); }
     return u0;
+}
+
+// Degree 0 near an axis has footprint ramps of width b, which can be far
+// narrower than one float ulp of u.  For that degree u_0 is carried as an
+// unevaluated sum hi + lo.
+struct U0DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ U0DF row_u0_df(const LineHdr &H, int dr, int k)
+{
+    float fr = (float)dr, fk = (float)k;
+    float big = __fsub_rn(__fmul_rn(fr, H.rho_hi), __fmul_rn(fk, H.a_hi));   // exact
+    float small = __fadd_rn(__fmaf_rn(fr, H.rho_lo, __fmul_rn(-fk, H.a_lo)), H.U0_lo);
+    float s = __fadd_rn(H.U0, big);                                             // two-sum
+    float bb = __fsub_rn(s, H.U0);
+    float err = __fadd_rn(__fsub_rn(H.U0, __fsub_rn(s, bb)), __fsub_rn(big, bb));
+    float lo = __fadd_rn(err, small);
+    float hi = __fadd_rn(s, lo);
+    lo = __fsub_rn(lo, __fsub_rn(hi, s));
+    return U0DF{hi, lo};
+}
+
+// u_0 - c for a float c, as one float (accurate when the result is small).
+__device__ __forceinline__ float df_minus(U0DF u, float c) { return __fadd_rn(__fsub_rn(u.hi, c), u.lo); }
+
+__device__ __forceinline__ U0DF row_start_df(const LineHdr &H, float inv_a, int r, int &k)
+{
+    int dr = r - H.r_ref;
+    float V = __fmaf_rn((float)dr, H.rho_hi + H.rho_lo, H.U0);
+    k = (int)ceilf(V * inv_a) - 1;
+    U0DF u = row_u0_df(H, dr, k);
+    // u_0 in (0, |kappa|], |kappa| = a_hi + a_lo
+    if (__fadd_rn(u.hi, u.lo) <= 0.0f) { k -= 1; u = row_u0_df(H, dr, k); }
+    else if (__fadd_rn(__fsub_rn(u.hi, H.a_hi), __fsub_rn(u.lo, H.a_lo)) > 0.0f) {
+        k += 1;
+        u = row_u0_df(H, dr, k);
+    }
+    return u;
 }
 
 // Kernel launchers (kernels.cu).

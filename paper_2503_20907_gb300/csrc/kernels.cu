@@ -77,12 +77,15 @@ __device__ void line_geometry(const LinesDev &L, int64_t r, double &dx, double &
     }
 }
 
-// The footprint parameters a, b as the table uses them.
-__device__ __forceinline__ void footprint_ab(double dx, double dy, float &af, float &bf)
+// The footprint parameters a, b as the table uses them.  For degree >= 1 a
+// b below kBMin changes phi by less than about 2 kBMin and is taken as the
+// Dirac of Prop. 1; degree 0 keeps any representable b (its ramps have slope
+// 1/(a b), so dropping b would move mass by O(1) near cell edges).
+__device__ __forceinline__ void footprint_ab(int degree, double dx, double dy, float &af, float &bf)
 {
     af = (float)fmax(fabs(dx), fabs(dy));
     bf = (float)fmin(fabs(dx), fabs(dy));
-    if (bf < kBMin) bf = 0.f;
+    if (bf < (degree == 0 ? 1e-30f : kBMin)) bf = 0.f;
 }
 
 __device__ __forceinline__ float two_w_of(int m, float af, float bf)
@@ -118,10 +121,11 @@ __global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, int64_t M)
     line_geometry(L, r, dx, dy, px, py);
     const int m = g.degree + 1;
     LineHdr H;
-    H.pad[0] = H.pad[1] = 0.f;
+    H.U0_lo = 0.f;
+    H.a_corr = 0.f;
     H.tab = (L.kind == SP_LINES_PARALLEL) ? (int)(r / L.n_det) : (int)r;
     float af, bf;
-    footprint_ab(dx, dy, af, bf);
+    footprint_ab(g.degree, dx, dy, af, bf);
     H.two_w = two_w_of(m, af, bf);
     H.K = slots_of(m, af, bf, H.two_w);
     const bool vert = fabs(dy) >= fabs(dx);
@@ -135,7 +139,8 @@ __global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, int64_t M)
     if (vert) { kap = -dy; rho = dx; rc = jc; qc = ic; Nr = g.ny; Nq = g.nx; }
     else { kap = dx; rho = -dy; rc = ic; qc = jc; Nr = g.nx; Nq = g.ny; }
     const int sgn = kap > 0.0 ? 1 : -1;
-    const double w = 0.5 * (double)H.two_w;
+    // w exactly as the table sees it, m (a + b)/2 with the table's a and b
+    const double w = 0.5 * (double)m * ((double)af + (double)bf);
     int flags = (vert ? kVert : 0) | (sgn < 0 ? kKapNeg : 0);
     if (g.degree == 0 && B == 0.0) flags |= kDeg0Axis;
 
@@ -175,9 +180,11 @@ __global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, int64_t M)
     while ((1 << nb) <= maxc) ++nb;
     const int bits = 23 - nb;
     H.U0 = (float)U0;
+    H.U0_lo = (float)(U0 - (double)H.U0);
     split_hi_lo(rho, bits, H.rho_hi, H.rho_lo);
     split_hi_lo(A, bits, H.a_hi, H.a_lo);
-    H.a = (float)A;
+    H.a = af;
+    H.a_corr = (float)(A - (double)af);
     H.r_ref = r_ref;
     H.q_ref = (int)qr;
     H.r_begin = rb;
@@ -221,6 +228,8 @@ __device__ void build_table(int n, float a, float b, float *out)
     if (b == 0.f) {
         // Dirac factor (Prop. 1): phi(u) = beta^n(u/a)/a on the a-knots.
         for (int q = 0; q < kTabHead; ++q) out[q] = (q < m) ? a : FLT_MAX;
+        out[kTabA] = a;
+        out[kTabB] = 0.f;
         for (int i = 0; i < m; ++i) {
             float sc = ainv;
             for (int e = 0; e <= n; ++e) {
@@ -268,7 +277,7 @@ __device__ void build_table(int n, float a, float b, float *out)
             } else {
                 float v = __fmaf_rn((float)(p0 - pp), a, (float)q0 * b);
                 if (v < 0.f) continue;
-                float t = v * binv;
+                float t = __fdiv_rn(v, b);   // exact when v is a multiple of b
                 l = (int)floorf(t);
                 if (l < 0 || l >= m) continue;
                 tau = t - (float)l;
@@ -305,6 +314,8 @@ __device__ void build_table(int n, float a, float b, float *out)
         sv[t] = r; sq[t] = q; sf[t] = f;
     }
     for (int q = 0; q < kTabHead; ++q) out[q] = (q < m) ? sv[q + 1] : FLT_MAX;
+    out[kTabA] = a;
+    out[kTabB] = b;
     const int K = slots_of(m, a, b, two_w);
     for (int sg = 0; sg <= m; ++sg) {
         const float hw = 0.5f * (((sg < m) ? sv[sg + 1] : a) - sv[sg]);
@@ -345,7 +356,7 @@ __global__ void tables_kernel(GridDev g, LinesDev L, float *tabs, int64_t n_tab)
         line_geometry(L, t, dx, dy, px, py);
     }
     float af, bf;
-    footprint_ab(dx, dy, af, bf);
+    footprint_ab(g.degree, dx, dy, af, bf);
     build_table(g.degree, af, bf, tabs + t * (int64_t)kTabFloats);
 }
 
@@ -379,6 +390,37 @@ struct RowCtx {
     const float *T;   // table row of the interval
 };
 
+// Row r of a line: first column q0, interval sigma, polynomial argument t of
+// candidate 0, and for degree 0 the argument shift per candidate and the
+// midpoint tie of an axis-aligned rectangle.
+struct RowEval {
+    int q0, sg;
+    float t;
+    bool tie;
+};
+
+template <int DEG>
+__device__ __forceinline__ RowEval row_eval(const LineHdr &H, const float *s, float inv_a, int sgn, int r)
+{
+    RowEval e;
+    int k;
+    if constexpr (DEG == 0) {
+        U0DF u = row_start_df(H, inv_a, r, k);
+        e.sg = (df_minus(u, s[0]) > 0.f) ? 1 : 0;
+        e.t = df_minus(u, e.sg ? s[0] : 0.f);
+        e.tie = (H.flags & kDeg0Axis) &&
+                __fadd_rn(__fsub_rn(u.hi, H.a_hi), __fsub_rn(u.lo, H.a_lo)) == 0.f;
+    } else {
+        float u0 = row_start(H, inv_a, r, k);
+        float s_lo;
+        e.sg = sigma_of<DEG>(s, u0, s_lo);
+        e.t = u0 - s_lo;
+        e.tie = false;
+    }
+    e.q0 = H.q_ref - sgn * k;
+    return e;
+}
+
 // Visit every candidate of every row of one line; `op(node, phi)` is called
 // for in-grid candidates (phi may be 0 beyond the support).
 template <int DEG, typename Op>
@@ -393,30 +435,43 @@ __device__ __forceinline__ void walk_line(const LineHdr &H, const float *tab, co
 #pragma unroll
     for (int q = 0; q <= DEG; ++q) s[q] = tab[q];
     for (int r = H.r_begin + lane; r < H.r_end; r += 32) {
-        int k;
-        float u0 = row_start(H, inv_a, r, k);
-        float s_lo;
-        int sg = sigma_of<DEG>(s, u0, s_lo);
-        float t = u0 - s_lo;
-        const float *T = tab + kTabHead + sg * kSigStride;
-        int q0 = H.q_ref - sgn * k;
+        const RowEval e = row_eval<DEG>(H, s, inv_a, sgn, r);
+        const float *T = tab + kTabHead + e.sg * kSigStride;
         for (int i = 0; i < H.K; ++i) {
-            int q = q0 + sgn * i;
+            int q = e.q0 + sgn * i;
             if ((unsigned)q < (unsigned)Nq) {
-                float phi = horner<DEG>(T + i * kNC, t);
-                if (DEG == 0 && (H.flags & kDeg0Axis) && u0 == H.a) phi = 0.5f * phi;
+                float ti = (DEG == 0) ? __fmaf_rn((float)i, H.a_corr, e.t) : e.t;
+                float phi = horner<DEG>(T + i * kNC, ti);
+                if (DEG == 0 && e.tie) phi = 0.5f * phi;
                 int node = vert ? r * g.nx + q : q * g.nx + r;
                 op(node, phi);
             }
         }
-        if (DEG == 0 && (H.flags & kDeg0Axis) && u0 == H.a) {
+        if (DEG == 0 && e.tie) {
             // the run also starts at u = 0: midpoint value on that edge too
-            int q = q0 - sgn;
+            int q = e.q0 - sgn;
             if ((unsigned)q < (unsigned)Nq) {
                 int node = vert ? r * g.nx + q : q * g.nx + r;
                 op(node, 0.5f * inv_a);
             }
         }
+    }
+}
+
+// Is candidate i of a row in the support (u_0 + i a < 2w; <= for ties)?
+template <int DEG>
+__device__ __forceinline__ bool candidate_in(const LineHdr &H, const float *s, const RowEval &e, int i,
+                                             float bf)
+{
+    if constexpr (DEG == 0) {
+        // u_0 = s_sigma + t; u_0 + i|kappa| - (a + b), formed to keep its sign exact
+        float base = e.sg ? s[0] : 0.f;
+        float d = __fadd_rn(__fsub_rn(base, (float)(1 - i) * H.a),
+                            __fsub_rn(__fmaf_rn((float)i, H.a_corr, e.t), bf));
+        return (H.flags & kDeg0Axis) ? d <= 0.f : d < 0.f;
+    } else {
+        float u0 = (e.sg ? s[e.sg - 1] : 0.f) + e.t;
+        return __fmaf_rn((float)i, H.a, u0) < H.two_w;
     }
 }
 
@@ -483,29 +538,29 @@ __global__ void visited_kernel(GridDev g, const LineHdr *__restrict__ hdr,
         const LineHdr H = hdr[line];
         int total = 0;
         if (!(H.flags & kEmpty)) {
+            const float *tab = tabs + (int64_t)H.tab * kTabFloats;
             const bool vert = H.flags & kVert;
             const int sgn = (H.flags & kKapNeg) ? -1 : 1;
             const int Nq = vert ? g.nx : g.ny;
             const float inv_a = 1.0f / H.a;
-            const bool ties = (DEG == 0) && (H.flags & kDeg0Axis);
-            int64_t base = offsets ? offsets[line] : 0;
+            // b of the table: 2w = m (a + b)
+            const float bf = tab[kTabB];   // b the table was built with
+            float s[DEG + 1];
+#pragma unroll
+            for (int q = 0; q <= DEG; ++q) s[q] = tab[q];
+            const int64_t base = offsets ? offsets[line] : 0;
             // rows in rounds of 32 so that every lane's writes have a place
             for (int r0 = H.r_begin; r0 < H.r_end; r0 += 32) {
-                int r = r0 + lane;
-                int cnt = 0, k = 0, q0 = 0;
-                float u0 = 0.f;
-                bool tie = false;
+                const int r = r0 + lane;
+                int cnt = 0;
+                RowEval e{0, 0, 0.f, false};
                 if (r < H.r_end) {
-                    u0 = row_start(H, inv_a, r, k);
-                    q0 = H.q_ref - sgn * k;
-                    tie = ties && u0 == H.a;
+                    e = row_eval<DEG>(H, s, inv_a, sgn, r);
                     for (int i = 0; i < H.K; ++i) {
-                        int q = q0 + sgn * i;
-                        float u = __fmaf_rn((float)i, H.a, u0);
-                        bool in = ties ? (u <= H.two_w) : (u < H.two_w);
-                        if ((unsigned)q < (unsigned)Nq && in) ++cnt;
+                        int q = e.q0 + sgn * i;
+                        if ((unsigned)q < (unsigned)Nq && candidate_in<DEG>(H, s, e, i, bf)) ++cnt;
                     }
-                    if (tie && (unsigned)(q0 - sgn) < (unsigned)Nq) ++cnt;
+                    if (e.tie && (unsigned)(e.q0 - sgn) < (unsigned)Nq) ++cnt;
                 }
                 int incl = cnt;
 #pragma unroll
@@ -513,19 +568,17 @@ __global__ void visited_kernel(GridDev g, const LineHdr *__restrict__ hdr,
                     int v = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += v;
                 }
-                int excl = incl - cnt;
-                int round_total = __shfl_sync(0xffffffffu, incl, 31);
+                const int excl = incl - cnt;
+                const int round_total = __shfl_sync(0xffffffffu, incl, 31);
                 if (nodes && offsets && cnt > 0) {
                     int64_t pos = base + total + excl;
                     for (int i = 0; i < H.K; ++i) {
-                        int q = q0 + sgn * i;
-                        float u = __fmaf_rn((float)i, H.a, u0);
-                        bool in = ties ? (u <= H.two_w) : (u < H.two_w);
-                        if ((unsigned)q < (unsigned)Nq && in)
+                        int q = e.q0 + sgn * i;
+                        if ((unsigned)q < (unsigned)Nq && candidate_in<DEG>(H, s, e, i, bf))
                             nodes[pos++] = vert ? r * g.nx + q : q * g.nx + r;
                     }
-                    if (tie && (unsigned)(q0 - sgn) < (unsigned)Nq) {
-                        int q = q0 - sgn;
+                    if (e.tie && (unsigned)(e.q0 - sgn) < (unsigned)Nq) {
+                        int q = e.q0 - sgn;
                         nodes[pos++] = vert ? r * g.nx + q : q * g.nx + r;
                     }
                 }
@@ -554,26 +607,28 @@ __global__ void expand_kernel(LinesDev L, int64_t M, float *theta_out, float *y_
 template <int DEG>
 __device__ float footprint_from_table(const float *tab, float a, float b, float yt)
 {
+    // The offset is split in double so that the probe measures the table only.
     const int m = DEG + 1;
     const float two_w = two_w_of(m, a, b);
-    const float u = yt + 0.5f * two_w;
+    const double u = (double)yt + 0.5 * (double)m * ((double)a + (double)b);
     const bool ties = (DEG == 0) && (b == 0.f);
+    const double tw = (double)m * ((double)a + (double)b);
     if (ties) {
-        if (u < 0.f || u > two_w) return 0.f;
-        if (u == 0.f || u == two_w) return 0.5f / a;
-    } else if (u <= 0.f || u >= two_w) {
+        if (u < 0.0 || u > tw) return 0.f;
+        if (u == 0.0 || u == tw) return 0.5f / a;
+    } else if (u <= 0.0 || u >= tw) {
         return 0.f;
     }
-    int i = (int)ceilf(u / a) - 1;
-    if (i < 0) i = 0;
-    float u0 = __fmaf_rn(-(float)i, a, u);
-    if (u0 <= 0.f) { i -= 1; u0 = __fmaf_rn(-(float)i, a, u); }
-    else if (u0 > a) { i += 1; u0 = __fmaf_rn(-(float)i, a, u); }
+    int i = (int)ceil(u / (double)a) - 1;
+    double u0d = u - (double)i * (double)a;
+    if (u0d <= 0.0) { i -= 1; u0d += (double)a; }
+    else if (u0d > (double)a) { i += 1; u0d -= (double)a; }
     const int K = slots_of(m, a, b, two_w);
     if (i < 0 || i >= K) return 0.f;
     float s_lo;
+    const float u0 = (float)u0d;
     int sg = sigma_of<DEG>(tab, u0, s_lo);
-    return horner<DEG>(tab + kTabHead + sg * kSigStride + i * kNC, u0 - s_lo);
+    return horner<DEG>(tab + kTabHead + sg * kSigStride + i * kNC, (float)(u0d - (double)s_lo));
 }
 
 template <int DEG>
@@ -585,7 +640,7 @@ __global__ void footprint_eval_kernel(int64_t count, const float *theta, const f
     double s, c;
     sincos((double)theta[r], &s, &c);
     float af, bf;
-    footprint_ab(c, s, af, bf);
+    footprint_ab(DEG, c, s, af, bf);
     float *tab = scratch + r * (int64_t)kTabFloats;
     build_table(DEG, af, bf, tab);
     out[r] = footprint_from_table<DEG>(tab, af, bf, yt[r]);
