@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="fan512_cubic (the benchmark) or fan256_cubic (small profiling case)")
     return ap.parse_args()
 
 
@@ -187,7 +189,7 @@ def run_ours(args, rank, ws, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     props = torch.cuda.get_device_properties(dev)
-    wl = workloads.workload(WORKLOAD)
+    wl = workloads.workload(args.workload)
     geo = wl.geometry
     grid = sp.Grid(wl.n, wl.n, wl.degree, wl.h)
     view = torch.from_numpy(geo.view_angle).to(dev)
@@ -278,8 +280,9 @@ def run_ours(args, rank, ws, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * tmax / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": wl.n, "degree": wl.degree,
-                   "geometry": "fan 720 views x 768 bins, dso 1000, dod 500", "lines": M,
+        "config": {"workload": wl.name, "grid": wl.n, "degree": wl.degree,
+                   "geometry": f"fan {geo.n_view} views x {geo.n_det} bins, dso {geo.dso:g}, dod {geo.dod:g}",
+                   "lines": M,
                    "phantom": "30 seeded ellipses", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}"},
         "stage_ms": {"prepare": prep_ms, "fwd": fwd_ms, "adj": adj_ms},
@@ -296,7 +299,7 @@ def run_ours(args, rank, ws, local):
         "clocks": clocks,
         "wall_s": wall,
     }
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and wl.name == WORKLOAD:
         cb = oracle_sample(wl)
         cb.pop("seconds", None)
         line["cpu_baseline"] = cb

@@ -397,6 +397,7 @@ struct RowEval {
     int q0, sg;
     float t;
     bool tie;
+    float uhi, ulo;   // degree 0: u_0 as a float pair
 };
 
 template <int DEG>
@@ -410,12 +411,16 @@ __device__ __forceinline__ RowEval row_eval(const LineHdr &H, const float *s, fl
         e.t = df_minus(u, e.sg ? s[0] : 0.f);
         e.tie = (H.flags & kDeg0Axis) &&
                 __fadd_rn(__fsub_rn(u.hi, H.a_hi), __fsub_rn(u.lo, H.a_lo)) == 0.f;
+        e.uhi = u.hi;
+        e.ulo = u.lo;
     } else {
         float u0 = row_start(H, inv_a, r, k);
         float s_lo;
         e.sg = sigma_of<DEG>(s, u0, s_lo);
         e.t = u0 - s_lo;
         e.tie = false;
+        e.uhi = u0;
+        e.ulo = 0.f;
     }
     e.q0 = H.q_ref - sgn * k;
     return e;
@@ -464,10 +469,10 @@ __device__ __forceinline__ bool candidate_in(const LineHdr &H, const float *s, c
                                              float bf)
 {
     if constexpr (DEG == 0) {
-        // u_0 = s_sigma + t; u_0 + i|kappa| - (a + b), formed to keep its sign exact
-        float base = e.sg ? s[0] : 0.f;
-        float d = __fadd_rn(__fsub_rn(base, (float)(1 - i) * H.a),
-                            __fsub_rn(__fmaf_rn((float)i, H.a_corr, e.t), bf));
+        // u_0 + i|kappa| - (a + b) with u_0 = uhi + ulo and |kappa| = a + a_corr:
+        // (uhi - (1-i) a) is exact when it is small, the rest are small terms.
+        float d = __fadd_rn(__fsub_rn(e.uhi, (float)(1 - i) * H.a),
+                            __fsub_rn(__fmaf_rn((float)i, H.a_corr, e.ulo), bf));
         return (H.flags & kDeg0Axis) ? d <= 0.f : d < 0.f;
     } else {
         float u0 = (e.sg ? s[e.sg - 1] : 0.f) + e.t;
@@ -553,7 +558,7 @@ __global__ void visited_kernel(GridDev g, const LineHdr *__restrict__ hdr,
             for (int r0 = H.r_begin; r0 < H.r_end; r0 += 32) {
                 const int r = r0 + lane;
                 int cnt = 0;
-                RowEval e{0, 0, 0.f, false};
+                RowEval e{0, 0, 0.f, false, 0.f, 0.f};
                 if (r < H.r_end) {
                     e = row_eval<DEG>(H, s, inv_a, sgn, r);
                     for (int i = 0; i < H.K; ++i) {

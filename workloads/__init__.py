@@ -104,6 +104,8 @@ def workload(name: str) -> Workload:
     fan512_cubic        512 x 512, degree 3, fan: 720 views in [0, 2 pi),
                         768 bins of width 1 centred on the axis, dso 1000, dod 500.
     parallel256_cubic   256 x 256, degree 3, 360 angles in [0, pi), 384 offsets -192 + j.
+    fan256_cubic        fan512_cubic at half size (256 x 256, 360 views x 384 bins,
+                        dso 500, dod 250), a small case of the same kernels.
     """
     if name == "parallel64_linear":
         n = 64
@@ -117,6 +119,13 @@ def workload(name: str) -> Workload:
                        det0=-383.5, ddet=1.0, dso=1000.0, dod=500.0)
         coef = ellipse_phantom(n, 30, 1, radius=24.0 * s, axes=(2.0 * s, 16.0 * s))
         return Workload(name, n, 3, 1.0, geo, coef, 1)
+    if name == "fan256_cubic":
+        n = 256
+        s = n / 64.0
+        geo = Geometry("fan", view_angle=_angles(360, 2.0 * math.pi), n_det=384,
+                       det0=-191.5, ddet=1.0, dso=500.0, dod=250.0)
+        coef = ellipse_phantom(n, 30, 2, radius=24.0 * s, axes=(2.0 * s, 16.0 * s))
+        return Workload(name, n, 3, 1.0, geo, coef, 2)
     if name == "parallel256_cubic":
         n = 256
         s = n / 64.0
