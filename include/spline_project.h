@@ -170,6 +170,33 @@ int64_t spline_plan_lines(const sp_plan *plan);
 /* Free the plan and its device memory (synchronises the device first). */
 sp_status spline_plan_destroy(sp_plan *plan);
 
+/*
+ * Forward projection that allocates nothing (this entry point has no
+ * counterpart in the paper; it is the same computation as
+ * spline_project_fwd).
+ *
+ * For callers that cannot let the library allocate device memory: programs
+ * that reserve the device's memory up front for their own pool, where a
+ * foreign cudaMalloc fails or fragments it, and latency-bound pipelines that
+ * cannot take the device-wide synchronisation of cudaFree or of growing a
+ * cached workspace.  Its scratch (per-line records and footprint tables) is a
+ * fixed 48 MiB array in the library's device memory, which every GPU that
+ * loads the library holds until the process exits.  Calls neither cudaMalloc
+ * nor cudaFree.
+ *
+ * Limit: 64 bytes per line plus 1312 bytes per footprint table (one per line;
+ * one per view for SP_LINES_PARALLEL) must fit in 48 MiB, i.e. about 36,000
+ * lines with their own tables; larger lists return SP_EINVAL with the byte
+ * count in sp_last_error().  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls on a device share the one array, and every call
+ * rewrites the part it uses before reading it: calls that overlap on the GPU
+ * (other streams, or before the previous call's kernels finished) race.
+ * Arguments, outputs and errors as spline_project_fwd.
+ */
+sp_status spline_project_fwd_noalloc(const sp_grid *grid, const float *coef,
+                                     const sp_lines *lines, float *sino, void *stream);
+
 /* Free the cached workspace of the current device (synchronises the device). */
 sp_status sp_release_workspace(void);
 

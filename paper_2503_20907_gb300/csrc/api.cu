@@ -156,6 +156,15 @@ sp_status prepare(const spx::GridDev &g, const spx::LinesDev &L, cudaStream_t s,
 
 }  // namespace
 
+namespace spx {
+// For other translation units of the library: the same argument checks and
+// the same thread-local last-error message as the entry points above.
+sp_status check_grid_for(const sp_grid *g, GridDev *out) { return check_grid(g, out); }
+sp_status check_lines_for(const sp_lines *L, LinesDev *out) { return check_lines(L, out); }
+sp_status record_error(sp_status st, const std::string &msg) { return fail(st, msg); }
+void clear_error() { g_err.clear(); }
+}  // namespace spx
+
 extern "C" {
 
 int64_t sp_lines_count(const sp_lines *lines) { return count_lines(lines); }
