@@ -234,6 +234,7 @@ def run_ours(args, rank, ws, local):
     adj = [e[2].elapsed_time(e[3]) for e in evs]
     tot = sum(e[0].elapsed_time(e[3]) for e in evs) / 1000.0
     tmax = allreduce_max(tot, ws)
+    slow_rows = plan.slow_rows()
 
     # end to end through the public API with host buffers
     coef_h = torch.from_numpy(wl.coef).pin_memory()
@@ -287,6 +288,7 @@ def run_ours(args, rank, ws, local):
                    "parallelism": f"replicas x{ws}"},
         "stage_ms": {"prepare": prep_ms, "fwd": fwd_ms, "adj": adj_ms},
         "pairs_per_direction": pairs,
+        "slow_rows": slow_rows,
         "basis_evals_per_s": 2 * pairs * args.steps / (tot) if tot > 0 else None,
         "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,

@@ -167,6 +167,13 @@ sp_status spline_plan_fwd(const sp_plan *plan, const float *coef, float *sino, v
 sp_status spline_plan_adj(const sp_plan *plan, const float *sino, float *coef_out, void *stream);
 /* Number of lines of the plan (-1 if plan is NULL). */
 int64_t spline_plan_lines(const sp_plan *plan);
+/*
+ * Diagnostics of the plan's forward projections so far (synchronises):
+ * slow_rows = rows whose run of nodes fell outside the shared-memory window
+ * staged for their group of lines and were read from global memory instead
+ * (results are the same; only speed differs).
+ */
+sp_status spline_plan_stats(const sp_plan *plan, int64_t *slow_rows);
 /* Free the plan and its device memory (synchronises the device first). */
 sp_status spline_plan_destroy(sp_plan *plan);
 

@@ -43,7 +43,8 @@ class SplineError(RuntimeError):
 EXPORTED = ("sp_lines_count", "spline_project_fwd", "spline_project_adj", "spline_lines_expand",
             "spline_footprint_eval", "spline_visited", "sp_release_workspace", "sp_last_error",
             "sp_version", "spline_plan_create", "spline_plan_prepare", "spline_plan_fwd",
-            "spline_plan_adj", "spline_plan_lines", "spline_plan_destroy")
+            "spline_plan_adj", "spline_plan_lines", "spline_plan_destroy", "spline_plan_stats",
+            "spline_project_fwd_noalloc")
 
 
 def load(build_if_stale: bool = True) -> ctypes.CDLL:
@@ -77,6 +78,10 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
     lib.spline_plan_adj.argtypes = [P, P, P, P]
     lib.spline_plan_lines.restype = ctypes.c_int64
     lib.spline_plan_lines.argtypes = [P]
+    lib.spline_plan_stats.restype = st
+    lib.spline_plan_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.spline_project_fwd_noalloc.restype = st
+    lib.spline_project_fwd_noalloc.argtypes = [G, P, L, P, P]
     lib.spline_plan_destroy.restype = st
     lib.spline_plan_destroy.argtypes = [P]
     lib.sp_release_workspace.restype = st
@@ -279,6 +284,12 @@ class Plan:
             raise ValueError("coef_out must be a contiguous tensor of ny*nx values")
         _check(load().spline_plan_adj(self._h, p.data_ptr(), coef_out.data_ptr(), _stream(stream)))
         return coef_out
+
+    def slow_rows(self) -> int:
+        """Rows read from global memory because they fell outside the staged window."""
+        v = ctypes.c_int64(0)
+        _check(load().spline_plan_stats(self._h, ctypes.byref(v)))
+        return int(v.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -136,17 +136,48 @@ int64_t table_count(const spx::LinesDev &L)
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Line records and footprint tables for (grid, lines) in the workspace.
+// Scratch of the strip forward: transposed coefficients, then the slow-row counter.
+size_t extra_bytes(const spx::GridDev &g, const spx::LinesDev &L)
+{
+    return spx::strip_supported(g, L) ? spx::strip_scratch_bytes(g) + 256 : 0;
+}
+
+int *slow_counter(const spx::GridDev &g, void *extra)
+{
+    return reinterpret_cast<int *>(static_cast<char *>(extra) + align_up(spx::strip_scratch_bytes(g)));
+}
+
+// Forward projection with the best kernel for the geometry.
+cudaError_t run_fwd(const spx::GridDev &g, const spx::LinesDev &L, const spx::LineHdr *hdr, const float *tabs,
+                    void *extra, const float *coef, float *sino, cudaStream_t s)
+{
+    if (extra && spx::strip_supported(g, L))
+        return spx::launch_fwd_strip(g, L, hdr, tabs, coef, extra, sino, slow_counter(g, extra), s);
+    return spx::launch_fwd(g, hdr, tabs, L.m, coef, sino, s);
+}
+
+// Adjoint with the best kernel for the geometry (coef_out overwritten).
+cudaError_t run_adj(const spx::GridDev &g, const spx::LinesDev &L, const spx::LineHdr *hdr, const float *tabs,
+                    void *extra, const float *sino, float *coef_out, cudaStream_t s)
+{
+    if (extra && spx::strip_supported(g, L))
+        return spx::launch_adj_strip(g, L, hdr, tabs, sino, extra, coef_out, slow_counter(g, extra), s);
+    return spx::launch_adj(g, hdr, tabs, L.m, sino, coef_out, s);
+}
+
 sp_status prepare(const spx::GridDev &g, const spx::LinesDev &L, cudaStream_t s,
-                  spx::LineHdr **hdr, float **tabs)
+                  spx::LineHdr **hdr, float **tabs, void **extra = nullptr)
 {
     const int64_t nt = table_count(L);
     size_t hb = align_up(sizeof(spx::LineHdr) * (size_t)L.m);
     size_t tb = align_up(sizeof(float) * (size_t)spx::kTabFloats * (size_t)nt);
+    size_t xb = align_up(extra_bytes(g, L));
     void *ws = nullptr;
-    sp_status st = workspace(hb + tb + 256, &ws);
+    sp_status st = workspace(hb + tb + xb + 256, &ws);
     if (st != SP_OK) return st;
     *hdr = reinterpret_cast<spx::LineHdr *>(ws);
     *tabs = reinterpret_cast<float *>(static_cast<char *>(ws) + hb);
+    if (extra) *extra = xb ? static_cast<char *>(ws) + hb + tb : nullptr;
     cudaError_t e = spx::launch_setup(g, L, *hdr, s);
     if (e != cudaSuccess) return cuda_fail(e, "line setup");
     e = spx::launch_tables(g, L, *tabs, nt, s);
@@ -183,8 +214,9 @@ sp_status spline_project_fwd(const sp_grid *grid, const float *coef, const sp_li
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     spx::LineHdr *hdr;
     float *tabs;
-    if ((st = prepare(g, L, s, &hdr, &tabs)) != SP_OK) return st;
-    cudaError_t e = spx::launch_fwd(g, hdr, tabs, L.m, coef, sino, s);
+    void *extra = nullptr;
+    if ((st = prepare(g, L, s, &hdr, &tabs, &extra)) != SP_OK) return st;
+    cudaError_t e = run_fwd(g, L, hdr, tabs, extra, coef, sino, s);
     if (e != cudaSuccess) return cuda_fail(e, "forward projection");
     return SP_OK;
 }
@@ -207,8 +239,9 @@ sp_status spline_project_adj(const sp_grid *grid, const float *sino, const sp_li
     }
     spx::LineHdr *hdr;
     float *tabs;
-    if ((st = prepare(g, L, s, &hdr, &tabs)) != SP_OK) return st;
-    cudaError_t e = spx::launch_adj(g, hdr, tabs, L.m, sino, coef_out, s);
+    void *extra = nullptr;
+    if ((st = prepare(g, L, s, &hdr, &tabs, &extra)) != SP_OK) return st;
+    cudaError_t e = run_adj(g, L, hdr, tabs, extra, sino, coef_out, s);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint projection");
     return SP_OK;
 }
@@ -265,6 +298,7 @@ struct sp_plan {
     void *mem;
     spx::LineHdr *hdr;
     float *tabs;
+    void *extra;       // strip scratch (transposed coefficients, slow-row counter) or NULL
     bool prepared;
 };
 
@@ -283,9 +317,10 @@ sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     size_t hb = align_up(sizeof(spx::LineHdr) * (size_t)L.m);
     size_t tb = align_up(sizeof(float) * (size_t)spx::kTabFloats * (size_t)table_count(L));
+    size_t xb = align_up(extra_bytes(g, L));
     void *mem = nullptr;
-    if (hb + tb > 0) {
-        e = cudaMalloc(&mem, hb + tb);
+    if (hb + tb + xb > 0) {
+        e = cudaMalloc(&mem, hb + tb + xb);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(SP_ENOMEM, std::string("plan allocation failed: ") + cudaGetErrorString(e));
@@ -298,7 +333,16 @@ sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan
     p->mem = mem;
     p->hdr = reinterpret_cast<spx::LineHdr *>(mem);
     p->tabs = mem ? reinterpret_cast<float *>(static_cast<char *>(mem) + hb) : nullptr;
+    p->extra = (mem && xb) ? static_cast<char *>(mem) + hb + tb : nullptr;
     p->prepared = false;
+    if (p->extra) {
+        e = cudaMemset(slow_counter(g, p->extra), 0, sizeof(int));
+        if (e != cudaSuccess) {
+            cudaFree(mem);
+            delete p;
+            return cuda_fail(e, "cudaMemset");
+        }
+    }
     *plan = p;
     return SP_OK;
 }
@@ -324,8 +368,8 @@ sp_status spline_plan_fwd(const sp_plan *plan, const float *coef, float *sino, v
     if (!plan->prepared) return fail(SP_EINVAL, "plan not prepared");
     if (plan->L.m == 0) return SP_OK;
     if (!coef || !sino) return fail(SP_EINVAL, "coef/sino pointers are NULL");
-    cudaError_t e = spx::launch_fwd(plan->g, plan->hdr, plan->tabs, plan->L.m, coef, sino,
-                                    static_cast<cudaStream_t>(stream));
+    cudaError_t e = run_fwd(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, coef, sino,
+                            static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "forward projection");
 }
 
@@ -336,12 +380,25 @@ sp_status spline_plan_adj(const sp_plan *plan, const float *sino, float *coef_ou
     if (!plan->prepared) return fail(SP_EINVAL, "plan not prepared");
     if (!coef_out) return fail(SP_EINVAL, "coef_out pointer is NULL");
     if (plan->L.m > 0 && !sino) return fail(SP_EINVAL, "sino pointer is NULL");
-    cudaError_t e = spx::launch_adj(plan->g, plan->hdr, plan->tabs, plan->L.m, sino, coef_out,
-                                    static_cast<cudaStream_t>(stream));
+    cudaError_t e = run_adj(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, sino, coef_out,
+                            static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "adjoint projection");
 }
 
 int64_t spline_plan_lines(const sp_plan *plan) { return plan ? plan->L.m : -1; }
+
+sp_status spline_plan_stats(const sp_plan *plan, int64_t *slow_rows)
+{
+    g_err.clear();
+    if (!plan || !slow_rows) return fail(SP_EINVAL, "NULL argument");
+    *slow_rows = 0;
+    if (!plan->extra) return SP_OK;
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, slow_counter(plan->g, plan->extra), sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    *slow_rows = v;
+    return SP_OK;
+}
 
 sp_status spline_plan_destroy(sp_plan *plan)
 {

@@ -50,6 +50,15 @@ constexpr int kTabB = 7;                      // head slot of its b
 constexpr int kTabFloats = kTabHead + kMaxSig * kSigStride;   // 328 floats
 constexpr float kBMin = 1e-7f;                // below this b is taken as 0 (Dirac)
 
+// Offset of the polynomial of (interval sg, candidate i) in a table.
+// Candidates are stored in pairs (2p, 2p+1) interleaved coefficient by
+// coefficient, so coefficient d sits at offset + 2 d and a lane that
+// evaluates a pair loads both polynomials as packed pairs.
+__host__ __device__ constexpr int tab_poly(int sg, int i)
+{
+    return kTabHead + sg * kSigStride + (i >> 1) * (2 * kNC) + (i & 1);
+}
+
 enum LineFlags : int {
     kVert = 1,        // rows are x2 (index j), columns x1 (index i)
     kKapNeg = 2,      // u decreases with the column index
@@ -149,6 +158,74 @@ __device__ __forceinline__ U0DF row_start_df(const LineHdr &H, float inv_a, int 
     return u;
 }
 
+// ------------------------------------------------------------------ row evaluation
+// Horner scheme of a table polynomial (coefficients at stride 2, see tab_poly).
+template <int DEG>
+__device__ __forceinline__ float horner(const float *T, float t)
+{
+    constexpr int NC = 2 * DEG + 2;
+    float s = T[2 * (NC - 1)];
+#pragma unroll
+    for (int d = NC - 2; d >= 0; --d) s = __fmaf_rn(s, t, T[2 * d]);
+    return s;
+}
+
+template <int DEG>
+__device__ __forceinline__ int sigma_of(const float *s, float u0, float &s_lo)
+{
+    int sg = 0;
+    s_lo = 0.f;
+#pragma unroll
+    for (int q = 0; q <= DEG; ++q) {
+        float v = s[q];
+        if (v < u0) { sg = q + 1; s_lo = v; }
+    }
+    return sg;
+}
+
+// Row r of a line: first column q0, interval sigma, polynomial argument t of
+// candidate 0, and for degree 0 the argument shift per candidate and the
+// midpoint tie of an axis-aligned rectangle.
+struct RowEval {
+    int q0, sg;
+    float t;
+    bool tie;
+    float uhi, ulo;   // degree 0: u_0 as a float pair
+};
+
+template <int DEG>
+__device__ __forceinline__ RowEval row_eval(const LineHdr &H, const float *s, float inv_a, int sgn, int r)
+{
+    RowEval e;
+    int k;
+    if constexpr (DEG == 0) {
+        U0DF u = row_start_df(H, inv_a, r, k);
+        e.sg = (df_minus(u, s[0]) > 0.f) ? 1 : 0;
+        e.t = df_minus(u, e.sg ? s[0] : 0.f);
+        e.tie = (H.flags & kDeg0Axis) &&
+                __fadd_rn(__fsub_rn(u.hi, H.a_hi), __fsub_rn(u.lo, H.a_lo)) == 0.f;
+        e.uhi = u.hi;
+        e.ulo = u.lo;
+    } else {
+        float u0 = row_start(H, inv_a, r, k);
+        float s_lo;
+        e.sg = sigma_of<DEG>(s, u0, s_lo);
+        e.t = u0 - s_lo;
+        e.tie = false;
+        e.uhi = u0;
+        e.ulo = 0.f;
+    }
+    e.q0 = H.q_ref - sgn * k;
+    return e;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Kernel launchers (kernels.cu).
 cudaError_t launch_setup(const GridDev &g, const LinesDev &L, LineHdr *hdr, cudaStream_t s);
 cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int64_t n_tab,
@@ -161,6 +238,17 @@ cudaError_t launch_visited(const GridDev &g, const LineHdr *hdr, const float *ta
                            int32_t *counts, const int64_t *offsets, int32_t *nodes,
                            cudaStream_t s);
 cudaError_t launch_expand(const LinesDev &L, float *theta_out, float *y_out, cudaStream_t s);
+
+// Forward projection with coefficient strips in shared memory (strip.cu), for
+// parallel and fan beams of degree >= 1.  `scratch` holds strip_scratch_bytes;
+// `slow_rows` counts rows whose run fell outside the staged window.
+bool strip_supported(const GridDev &g, const LinesDev &L);
+size_t strip_scratch_bytes(const GridDev &g);
+cudaError_t launch_fwd_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
+                             const float *coef, void *scratch, float *sino, int *slow_rows, cudaStream_t s);
+// Adjoint with strip accumulators; coef_out is overwritten.
+cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
+                             const float *sino, void *scratch, float *coef_out, int *slow_rows, cudaStream_t s);
 cudaError_t launch_footprint_eval(int degree, int64_t count, const float *theta, const float *yt,
                                   float *out, float *scratch, cudaStream_t s);
 

@@ -14,7 +14,9 @@ namespace {
 // Left-anchored B-spline beta^n on [0, n+1] (Sec. III.C, centred beta^n
 // shifted by (n+1)/2), piece l on x = l + tau, tau in [0, 1): coefficients of
 // tau^0..tau^n, from beta^n(x) = 1/n! sum_k (-1)^k C(n+1,k) (x-k)_+^n.
-__constant__ float kBPiece[4][4][4] = {
+// Read with lane-dependent l, so it sits in global memory (L1), not in the
+// constant bank.
+__device__ const float kBPiece[4][4][4] = {
     {{1.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}},
     {{0.f, 1.f, 0.f, 0.f}, {1.f, -1.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}},
     {{0.f, 0.f, 0.5f, 0.f}, {0.5f, 1.f, -1.f, 0.f}, {0.5f, -1.f, 0.5f, 0.f}, {0.f, 0.f, 0.f, 0.f}},
@@ -22,12 +24,14 @@ __constant__ float kBPiece[4][4][4] = {
      {1.f / 6.f, -0.5f, 0.5f, -1.f / 6.f}},
 };
 
-__device__ __forceinline__ float binomf(int n, int k)
-{
-    float r = 1.f;
-    for (int i = 1; i <= k; ++i) r = r * (float)(n - k + i) / (float)i;
-    return r;
-}
+// Binomial coefficients C(k, d), k, d < 8 (Pascal's triangle).
+__constant__ float kBinom[8][8] = {
+    {1, 0, 0, 0, 0, 0, 0, 0},      {1, 1, 0, 0, 0, 0, 0, 0},       {1, 2, 1, 0, 0, 0, 0, 0},
+    {1, 3, 3, 1, 0, 0, 0, 0},      {1, 4, 6, 4, 1, 0, 0, 0},       {1, 5, 10, 10, 5, 1, 0, 0},
+    {1, 6, 15, 20, 15, 6, 1, 0},   {1, 7, 21, 35, 35, 21, 7, 1},
+};
+
+__device__ __forceinline__ float binomf(int n, int k) { return kBinom[n][k]; }
 
 __device__ __forceinline__ float factf(int n)
 {
@@ -217,134 +221,160 @@ __device__ __forceinline__ float sym_diff(int dp, int dq, float a, float b, floa
     return __fmaf_rn((float)dp, a, __fmaf_rn((float)dq, b, extra));
 }
 
-// Build the footprint table of one direction (see common.cuh).
-__device__ void build_table(int n, float a, float b, float *out)
+// Build the footprint table of one direction (see common.cuh), one warp per
+// table.  sm is this warp's shared scratch of kBuildScratch floats; the
+// table is assembled there and then written to out (if out is not NULL).
+constexpr int kBuildScratch = kTabFloats + 32 + 32 + 25 * 8 + 8 + 8 + 8;
+constexpr int kTabWarps = 8;
+
+__device__ void build_table_warp(int n, float a, float b, float *out, float *sm, int lane)
 {
     const int m = n + 1;
     const int nc = 2 * n + 2;
-    for (int k = 0; k < kTabFloats; ++k) out[k] = 0.f;
+    float *tab = sm;
+    float *bv = tab + kTabFloats;                       // sorted breakpoint values
+    int *bpq = reinterpret_cast<int *>(bv + 32);        // and their (p, q), p | q << 8
+    float *P = reinterpret_cast<float *>(bpq + 32);     // piece polynomials [25][8]
+    float *sv = P + 25 * 8;                             // sorted u_0 interval ends
+    int *sq = reinterpret_cast<int *>(sv + 8);
+    int *sf = sq + 8;
+    for (int k = lane; k < kTabFloats; k += 32) tab[k] = 0.f;
+    __syncwarp();
     const float two_w = two_w_of(m, a, b);
     const float ainv = 1.0f / a;
     if (b == 0.f) {
         // Dirac factor (Prop. 1): phi(u) = beta^n(u/a)/a on the a-knots.
-        for (int q = 0; q < kTabHead; ++q) out[q] = (q < m) ? a : FLT_MAX;
-        out[kTabA] = a;
-        out[kTabB] = 0.f;
-        for (int i = 0; i < m; ++i) {
+        if (lane < kTabHead) tab[lane] = lane == kTabA ? a : (lane == kTabB ? 0.f : (lane < m ? a : FLT_MAX));
+        if (lane < m * (n + 1)) {
+            const int i = lane / (n + 1), e = lane - i * (n + 1);
             float sc = ainv;
-            for (int e = 0; e <= n; ++e) {
-                out[kTabHead + i * kNC + e] = kBPiece[n][i][e] * sc;
-                sc *= ainv;
-            }
+            for (int k = 0; k < e; ++k) sc *= ainv;
+            tab[tab_poly(0, i) + 2 * e] = kBPiece[n][i][e] * sc;
         }
-        return;
-    }
-    // breakpoints p a + q b, sorted (ties by p, then q)
-    float bv[25];
-    signed char bpp[25], bpq[25];
-    int nbp = 0;
-    for (int p = 0; p <= m; ++p)
-        for (int q = 0; q <= m; ++q) {
-            float v = __fmaf_rn((float)p, a, (float)q * b);
-            int t = nbp++;
-            while (t > 0 && (bv[t - 1] > v || (bv[t - 1] == v && (bpp[t - 1] > p ||
-                                                                 (bpp[t - 1] == p && bpq[t - 1] > q))))) {
-                bv[t] = bv[t - 1]; bpp[t] = bpp[t - 1]; bpq[t] = bpq[t - 1];
-                --t;
-            }
-            bv[t] = v; bpp[t] = (signed char)p; bpq[t] = (signed char)q;
+    } else {
+        // breakpoints p a + q b, ranked (ties by p, then q)
+        const int NB = (m + 1) * (m + 1);
+        int p = 0, q = 0;
+        float v = 0.f;
+        if (lane < NB) {
+            p = lane / (m + 1);
+            q = lane - p * (m + 1);
+            v = __fmaf_rn((float)p, a, (float)q * b);
         }
-    // pieces that start at or before the centre w
-    int nh = 0;
-    while (nh < nbp && sym_diff(2 * bpp[nh] - m, 2 * bpq[nh] - m, a, b, 0.f) <= 0.f) ++nh;
-    if (nh < 1) nh = 1;
-
-    float P[25][8];
-    const float binv = 1.0f / b;
-    float am = 1.f;
-    for (int k = 0; k < m; ++k) am *= ainv;
-    for (int pi = 0; pi < nh; ++pi) {
-        const int p0 = bpp[pi], q0 = bpq[pi];
-        // derivatives n+1..2n+1 directly (right-sided at the breakpoint)
-        float hi[kMaxM];
-        for (int e = 0; e <= n; ++e) hi[e] = 0.f;
-        for (int pp = 0; pp <= m; ++pp) {
-            int l;
-            float tau;
-            if (pp == p0) {
-                if (q0 >= m) continue;
-                l = q0; tau = 0.f;
-            } else {
-                float v = __fmaf_rn((float)(p0 - pp), a, (float)q0 * b);
-                if (v < 0.f) continue;
-                float t = __fdiv_rn(v, b);   // exact when v is a multiple of b
-                l = (int)floorf(t);
-                if (l < 0 || l >= m) continue;
-                tau = t - (float)l;
-            }
-            float D[kMaxM];
-            bspline_piece_derivs(n, l, tau, binv, D);
-            float wp = binomf(m, pp) * ((pp & 1) ? -1.f : 1.f);
-            for (int e = 0; e <= n; ++e) hi[e] = __fmaf_rn(wp, D[e], hi[e]);
+        int rank = 0;
+        for (int j = 0; j < NB; ++j) {
+            const float vj = __shfl_sync(0xffffffffu, v, j);
+            const int pj = j / (m + 1), qj = j - pj * (m + 1);
+            rank += (vj < v) || (vj == v && (pj < p || (pj == p && qj < q)));
         }
-        for (int e = 0; e <= n; ++e) P[pi][n + 1 + e] = hi[e] * am / factf(n + 1 + e);
-        // derivatives 0..n carried from the previous piece
-        if (pi == 0) {
-            for (int d = 0; d <= n; ++d) P[0][d] = 0.f;
-        } else {
-            float dl = sym_diff(p0 - bpp[pi - 1], q0 - bpq[pi - 1], a, b, 0.f);
-            for (int d = 0; d <= n; ++d) {
-                float s = 0.f;
-                for (int k = nc - 1; k >= d; --k) s = __fmaf_rn(s, dl, binomf(k, d) * P[pi - 1][k]);
-                P[pi][d] = s;
+        if (lane < NB) { bv[rank] = v; bpq[rank] = p | (q << 8); }
+        __syncwarp();
+        // pieces that start at or before the centre w: the leading sorted run
+        int mp = 0, mq = 0;
+        if (lane < NB) { mp = bpq[lane] & 255; mq = bpq[lane] >> 8; }
+        const unsigned outside =
+            __ballot_sync(0xffffffffu, lane >= NB || sym_diff(2 * mp - m, 2 * mq - m, a, b, 0.f) > 0.f);
+        int nh = __ffs(outside) - 1;   // lane NB at the latest (NB <= 25)
+        if (nh < 1) nh = 1;
+        // derivatives n+1..2n+1 of every piece directly (right-sided at its start)
+        const float binv = 1.0f / b;
+        float am = 1.f;
+        for (int k = 0; k < m; ++k) am *= ainv;
+        if (lane < nh) {
+            const int p0 = mp, q0 = mq;
+            float hi[kMaxM];
+            for (int e = 0; e <= n; ++e) hi[e] = 0.f;
+            for (int pp = 0; pp <= m; ++pp) {
+                int l;
+                float tau;
+                if (pp == p0) {
+                    if (q0 >= m) continue;
+                    l = q0; tau = 0.f;
+                } else {
+                    const float vv = __fmaf_rn((float)(p0 - pp), a, (float)q0 * b);
+                    if (vv < 0.f) continue;
+                    const float t = __fdiv_rn(vv, b);   // exact when vv is a multiple of b
+                    l = (int)floorf(t);
+                    if (l < 0 || l >= m) continue;
+                    tau = t - (float)l;
+                }
+                float D[kMaxM];
+                bspline_piece_derivs(n, l, tau, binv, D);
+                const float wp = binomf(m, pp) * ((pp & 1) ? -1.f : 1.f);
+                for (int e = 0; e <= n; ++e) hi[e] = __fmaf_rn(wp, D[e], hi[e]);
             }
+            for (int e = 0; e <= n; ++e) P[lane * 8 + n + 1 + e] = hi[e] * am / factf(n + 1 + e);
+            if (lane == 0)
+                for (int d = 0; d <= n; ++d) P[d] = 0.f;
         }
-    }
-    // u_0 interval ends s_q = (q b) mod a in (0, a], sorted
-    float sv[kMaxSig];
-    int sq[kMaxSig], sf[kMaxSig];
-    sv[0] = 0.f; sq[0] = 0; sf[0] = 0;
-    for (int q = 1; q <= m; ++q) {
-        int f = (int)floorf((float)q * b * ainv);
-        float r = __fmaf_rn((float)(-f), a, (float)q * b);
-        if (r <= 0.f) { f -= 1; r = __fmaf_rn((float)(-f), a, (float)q * b); }
-        else if (r > a) { f += 1; r = __fmaf_rn((float)(-f), a, (float)q * b); }
-        int t = q;
-        while (t > 1 && sv[t - 1] > r) { sv[t] = sv[t - 1]; sq[t] = sq[t - 1]; sf[t] = sf[t - 1]; --t; }
-        sv[t] = r; sq[t] = q; sf[t] = f;
-    }
-    for (int q = 0; q < kTabHead; ++q) out[q] = (q < m) ? sv[q + 1] : FLT_MAX;
-    out[kTabA] = a;
-    out[kTabB] = b;
-    const int K = slots_of(m, a, b, two_w);
-    for (int sg = 0; sg <= m; ++sg) {
-        const float hw = 0.5f * (((sg < m) ? sv[sg + 1] : a) - sv[sg]);
-        for (int i = 0; i < K; ++i) {
+        __syncwarp();
+        // derivatives 0..n carried from piece to piece (lane d computes coefficient d)
+        for (int pi = 1; pi < nh; ++pi) {
+            if (lane <= n) {
+                const int cur = bpq[pi], prev = bpq[pi - 1];
+                const float dl = sym_diff((cur & 255) - (prev & 255), (cur >> 8) - (prev >> 8), a, b, 0.f);
+                float sacc = 0.f;
+                for (int k = nc - 1; k >= lane; --k) sacc = __fmaf_rn(sacc, dl, binomf(k, lane) * P[(pi - 1) * 8 + k]);
+                P[pi * 8 + lane] = sacc;
+            }
+            __syncwarp();
+        }
+        // u_0 interval ends s_q = (q b) mod a in (0, a], sorted (stable in q)
+        float rq = 0.f;
+        int fq = 0;
+        if (lane >= 1 && lane <= m) {
+            fq = (int)floorf((float)lane * b * ainv);
+            rq = __fmaf_rn((float)(-fq), a, (float)lane * b);
+            if (rq <= 0.f) { fq -= 1; rq = __fmaf_rn((float)(-fq), a, (float)lane * b); }
+            else if (rq > a) { fq += 1; rq = __fmaf_rn((float)(-fq), a, (float)lane * b); }
+        }
+        int srank = 1;
+        for (int j = 1; j <= m; ++j) {
+            const float rj = __shfl_sync(0xffffffffu, rq, j);
+            srank += (j < lane) ? (rj <= rq) : (j > lane ? (rj < rq) : 0);
+        }
+        if (lane >= 1 && lane <= m) { sv[srank] = rq; sq[srank] = lane; sf[srank] = fq; }
+        if (lane == 0) { sv[0] = 0.f; sq[0] = 0; sf[0] = 0; }
+        __syncwarp();
+        if (lane < kTabHead) tab[lane] = lane == kTabA ? a : (lane == kTabB ? b : (lane < m ? sv[lane + 1] : FLT_MAX));
+        const int K = slots_of(m, a, b, two_w);
+        for (int idx = lane; idx < (m + 1) * K; idx += 32) {
+            const int sg = idx / K, i = idx - sg * K;
+            const float hw = 0.5f * (((sg < m) ? sv[sg + 1] : a) - sv[sg]);
             // interval start u_lo = (i - f) a + q b; midpoint u_lo + hw
             const int pl = i - sf[sg], ql = sq[sg];
             if (sym_diff(pl - m, ql - m, a, b, hw) >= 0.f) continue;          // beyond 2w
             const bool mirror = sym_diff(2 * pl - m, 2 * ql - m, a, b, 2.f * hw) > 0.f;
             int pi = 0;
             if (!mirror) {
-                while (pi + 1 < nh && sym_diff(pl - bpp[pi + 1], ql - bpq[pi + 1], a, b, hw) >= 0.f) ++pi;
+                while (pi + 1 < nh && sym_diff(pl - (bpq[pi + 1] & 255), ql - (bpq[pi + 1] >> 8), a, b, hw) >= 0.f) ++pi;
             } else {
-                while (pi + 1 < nh && sym_diff(m - pl - bpp[pi + 1], m - ql - bpq[pi + 1], a, b, -hw) >= 0.f) ++pi;
+                while (pi + 1 < nh &&
+                       sym_diff(m - pl - (bpq[pi + 1] & 255), m - ql - (bpq[pi + 1] >> 8), a, b, -hw) >= 0.f)
+                    ++pi;
             }
-            float X = mirror ? sym_diff(m - pl - bpp[pi], m - ql - bpq[pi], a, b, 0.f)
-                             : sym_diff(pl - bpp[pi], ql - bpq[pi], a, b, 0.f);
-            float *T = out + kTabHead + sg * kSigStride + i * kNC;
+            const int bp = bpq[pi] & 255, bq = bpq[pi] >> 8;
+            const float X = mirror ? sym_diff(m - pl - bp, m - ql - bq, a, b, 0.f) : sym_diff(pl - bp, ql - bq, a, b, 0.f);
+            float *T = tab + tab_poly(sg, i);
             for (int d = 0; d < nc; ++d) {
-                float s = 0.f;
-                for (int k = nc - 1; k >= d; --k) s = __fmaf_rn(s, X, binomf(k, d) * P[pi][k]);
-                T[d] = (mirror && (d & 1)) ? -s : s;
+                float sacc = 0.f;
+                for (int k = nc - 1; k >= d; --k) sacc = __fmaf_rn(sacc, X, binomf(k, d) * P[pi * 8 + k]);
+                T[2 * d] = (mirror && (d & 1)) ? -sacc : sacc;
             }
         }
     }
+    __syncwarp();
+    if (out)
+        for (int k = lane; k < kTabFloats / 4; k += 32)
+            reinterpret_cast<float4 *>(out)[k] = reinterpret_cast<const float4 *>(tab)[k];
+    __syncwarp();
 }
 
-__global__ void tables_kernel(GridDev g, LinesDev L, float *tabs, int64_t n_tab)
+__global__ void __launch_bounds__(kTabWarps * 32) tables_kernel(GridDev g, LinesDev L, float *tabs, int64_t n_tab)
 {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ __align__(16) float scratch[kTabWarps][kBuildScratch];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * kTabWarps + warp;
     if (t >= n_tab) return;
     double dx, dy;
     if (L.kind == SP_LINES_PARALLEL) {
@@ -357,75 +387,10 @@ __global__ void tables_kernel(GridDev g, LinesDev L, float *tabs, int64_t n_tab)
     }
     float af, bf;
     footprint_ab(g.degree, dx, dy, af, bf);
-    build_table(g.degree, af, bf, tabs + t * (int64_t)kTabFloats);
+    build_table_warp(g.degree, af, bf, tabs + t * (int64_t)kTabFloats, scratch[warp], lane);
 }
 
 // ------------------------------------------------------------------ evaluation
-template <int DEG>
-__device__ __forceinline__ float horner(const float *T, float t)
-{
-    constexpr int NC = 2 * DEG + 2;
-    float s = T[NC - 1];
-#pragma unroll
-    for (int d = NC - 2; d >= 0; --d) s = __fmaf_rn(s, t, T[d]);
-    return s;
-}
-
-template <int DEG>
-__device__ __forceinline__ int sigma_of(const float *s, float u0, float &s_lo)
-{
-    int sg = 0;
-    s_lo = 0.f;
-#pragma unroll
-    for (int q = 0; q <= DEG; ++q) {
-        float v = s[q];
-        if (v < u0) { sg = q + 1; s_lo = v; }
-    }
-    return sg;
-}
-
-struct RowCtx {
-    int k, q0, sgn;
-    float u0, t;
-    const float *T;   // table row of the interval
-};
-
-// Row r of a line: first column q0, interval sigma, polynomial argument t of
-// candidate 0, and for degree 0 the argument shift per candidate and the
-// midpoint tie of an axis-aligned rectangle.
-struct RowEval {
-    int q0, sg;
-    float t;
-    bool tie;
-    float uhi, ulo;   // degree 0: u_0 as a float pair
-};
-
-template <int DEG>
-__device__ __forceinline__ RowEval row_eval(const LineHdr &H, const float *s, float inv_a, int sgn, int r)
-{
-    RowEval e;
-    int k;
-    if constexpr (DEG == 0) {
-        U0DF u = row_start_df(H, inv_a, r, k);
-        e.sg = (df_minus(u, s[0]) > 0.f) ? 1 : 0;
-        e.t = df_minus(u, e.sg ? s[0] : 0.f);
-        e.tie = (H.flags & kDeg0Axis) &&
-                __fadd_rn(__fsub_rn(u.hi, H.a_hi), __fsub_rn(u.lo, H.a_lo)) == 0.f;
-        e.uhi = u.hi;
-        e.ulo = u.lo;
-    } else {
-        float u0 = row_start(H, inv_a, r, k);
-        float s_lo;
-        e.sg = sigma_of<DEG>(s, u0, s_lo);
-        e.t = u0 - s_lo;
-        e.tie = false;
-        e.uhi = u0;
-        e.ulo = 0.f;
-    }
-    e.q0 = H.q_ref - sgn * k;
-    return e;
-}
-
 // Visit every candidate of every row of one line; `op(node, phi)` is called
 // for in-grid candidates (phi may be 0 beyond the support).
 template <int DEG, typename Op>
@@ -441,12 +406,11 @@ __device__ __forceinline__ void walk_line(const LineHdr &H, const float *tab, co
     for (int q = 0; q <= DEG; ++q) s[q] = tab[q];
     for (int r = H.r_begin + lane; r < H.r_end; r += 32) {
         const RowEval e = row_eval<DEG>(H, s, inv_a, sgn, r);
-        const float *T = tab + kTabHead + e.sg * kSigStride;
         for (int i = 0; i < H.K; ++i) {
             int q = e.q0 + sgn * i;
             if ((unsigned)q < (unsigned)Nq) {
                 float ti = (DEG == 0) ? __fmaf_rn((float)i, H.a_corr, e.t) : e.t;
-                float phi = horner<DEG>(T + i * kNC, ti);
+                float phi = horner<DEG>(tab + tab_poly(e.sg, i), ti);
                 if (DEG == 0 && e.tie) phi = 0.5f * phi;
                 int node = vert ? r * g.nx + q : q * g.nx + r;
                 op(node, phi);
@@ -478,13 +442,6 @@ __device__ __forceinline__ bool candidate_in(const LineHdr &H, const float *s, c
         float u0 = (e.sg ? s[e.sg - 1] : 0.f) + e.t;
         return __fmaf_rn((float)i, H.a, u0) < H.two_w;
     }
-}
-
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 template <int DEG>
@@ -633,22 +590,22 @@ __device__ float footprint_from_table(const float *tab, float a, float b, float 
     float s_lo;
     const float u0 = (float)u0d;
     int sg = sigma_of<DEG>(tab, u0, s_lo);
-    return horner<DEG>(tab + kTabHead + sg * kSigStride + i * kNC, (float)(u0d - (double)s_lo));
+    return horner<DEG>(tab + tab_poly(sg, i), (float)(u0d - (double)s_lo));
 }
 
 template <int DEG>
-__global__ void footprint_eval_kernel(int64_t count, const float *theta, const float *yt,
-                                      float *out, float *scratch)
+__global__ void footprint_eval_kernel(int64_t count, const float *theta, const float *yt, float *out)
 {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ __align__(16) float scratch[kTabWarps][kBuildScratch];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * kTabWarps + warp;
     if (r >= count) return;
     double s, c;
     sincos((double)theta[r], &s, &c);
     float af, bf;
     footprint_ab(DEG, c, s, af, bf);
-    float *tab = scratch + r * (int64_t)kTabFloats;
-    build_table(DEG, af, bf, tab);
-    out[r] = footprint_from_table<DEG>(tab, af, bf, yt[r]);
+    build_table_warp(DEG, af, bf, nullptr, scratch[warp], lane);
+    if (lane == 0) out[r] = footprint_from_table<DEG>(scratch[warp], af, bf, yt[r]);
 }
 
 inline unsigned blocks_for(int64_t n, int per)
@@ -678,7 +635,7 @@ cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int6
                           cudaStream_t s)
 {
     if (n_tab <= 0) return cudaSuccess;
-    tables_kernel<<<blocks_for(n_tab, 64), 64, 0, s>>>(g, L, tabs, n_tab);
+    tables_kernel<<<blocks_for(n_tab, kTabWarps), kTabWarps * 32, 0, s>>>(g, L, tabs, n_tab);
     return cudaGetLastError();
 }
 
@@ -728,8 +685,9 @@ cudaError_t launch_footprint_eval(int degree, int64_t count, const float *theta,
                                   float *out, float *scratch, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
-    SPX_DISPATCH(degree, footprint_eval_kernel, blocks_for(count, 64), 64, s, count, theta, yt,
-                 out, scratch);
+    (void)scratch;
+    SPX_DISPATCH(degree, footprint_eval_kernel, blocks_for(count, kTabWarps), kTabWarps * 32, s, count, theta, yt,
+                 out);
     return cudaGetLastError();
 }
 
