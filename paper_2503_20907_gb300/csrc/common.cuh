@@ -227,7 +227,7 @@ __device__ __forceinline__ float warp_sum(float v)
 }
 
 // Kernel launchers (kernels.cu).
-cudaError_t launch_setup(const GridDev &g, const LinesDev &L, LineHdr *hdr, cudaStream_t s);
+cudaError_t launch_setup(const GridDev &g, const LinesDev &L, LineHdr *hdr, float *tabs, cudaStream_t s);
 cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int64_t n_tab,
                           cudaStream_t s);
 cudaError_t launch_fwd(const GridDev &g, const LineHdr *hdr, const float *tabs, int64_t m,

@@ -117,7 +117,7 @@ __device__ void split_hi_lo(double x, int bits, float &hi, float &lo)
 }
 
 // ------------------------------------------------------------------ setup
-__global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, int64_t M)
+__global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, float *tabs, int64_t M)
 {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= M) return;
@@ -130,6 +130,11 @@ __global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, int64_t M)
     H.tab = (L.kind == SP_LINES_PARALLEL) ? (int)(r / L.n_det) : (int)r;
     float af, bf;
     footprint_ab(g.degree, dx, dy, af, bf);
+    if (L.kind != SP_LINES_PARALLEL || r % L.n_det == 0) {
+        // the owner of table H.tab hands a and b to the table builder
+        tabs[(int64_t)H.tab * kTabFloats + kTabA] = af;
+        tabs[(int64_t)H.tab * kTabFloats + kTabB] = bf;
+    }
     H.two_w = two_w_of(m, af, bf);
     H.K = slots_of(m, af, bf, H.two_w);
     const bool vert = fabs(dy) >= fabs(dx);
@@ -198,16 +203,20 @@ __global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, int64_t M)
 }
 
 // ------------------------------------------------------------------ tables
-// Derivatives e = 0..n of B-spline piece l at tau, times b^-(1+e).
-__device__ __forceinline__ void bspline_piece_derivs(int n, int l, float tau, float binv, float *D)
+// Derivatives e = 0..N of B-spline piece l at tau, times b^-(1+e).
+template <int N>
+__device__ __forceinline__ void bspline_piece_derivs(int l, float tau, float binv, float *D)
 {
     float sc = binv;
-    for (int e = 0; e <= n; ++e) {
+#pragma unroll
+    for (int e = 0; e <= N; ++e) {
         float acc = 0.f;
-        for (int k = n; k >= e; --k) {
+#pragma unroll
+        for (int k = N; k >= e; --k) {
             float ff = 1.f;   // k!/(k-e)!
+#pragma unroll
             for (int t = 0; t < e; ++t) ff *= (float)(k - t);
-            acc = acc * tau + kBPiece[n][l][k] * ff;
+            acc = acc * tau + kBPiece[N][l][k] * ff;
         }
         D[e] = acc * sc;
         sc *= binv;
@@ -222,15 +231,15 @@ __device__ __forceinline__ float sym_diff(int dp, int dq, float a, float b, floa
 }
 
 // Build the footprint table of one direction (see common.cuh), one warp per
-// table.  sm is this warp's shared scratch of kBuildScratch floats; the
-// table is assembled there and then written to out (if out is not NULL).
+// table, degree N.  sm is this warp's shared scratch of kBuildScratch floats;
+// the table is assembled there and then written to out (if out is not NULL).
 constexpr int kBuildScratch = kTabFloats + 32 + 32 + 25 * 8 + 8 + 8 + 8;
 constexpr int kTabWarps = 8;
 
-__device__ void build_table_warp(int n, float a, float b, float *out, float *sm, int lane)
+template <int N>
+__device__ void build_table_warp(float a, float b, float *out, float *sm, int lane)
 {
-    const int m = n + 1;
-    const int nc = 2 * n + 2;
+    constexpr int n = N, m = N + 1, nc = 2 * N + 2;
     float *tab = sm;
     float *bv = tab + kTabFloats;                       // sorted breakpoint values
     int *bpq = reinterpret_cast<int *>(bv + 32);        // and their (p, q), p | q << 8
@@ -253,7 +262,7 @@ __device__ void build_table_warp(int n, float a, float b, float *out, float *sm,
         }
     } else {
         // breakpoints p a + q b, ranked (ties by p, then q)
-        const int NB = (m + 1) * (m + 1);
+        constexpr int NB = (m + 1) * (m + 1);
         int p = 0, q = 0;
         float v = 0.f;
         if (lane < NB) {
@@ -262,9 +271,11 @@ __device__ void build_table_warp(int n, float a, float b, float *out, float *sm,
             v = __fmaf_rn((float)p, a, (float)q * b);
         }
         int rank = 0;
+#pragma unroll
         for (int j = 0; j < NB; ++j) {
             const float vj = __shfl_sync(0xffffffffu, v, j);
-            const int pj = j / (m + 1), qj = j - pj * (m + 1);
+            constexpr int M1 = m + 1;
+            const int pj = j / M1, qj = j - pj * M1;
             rank += (vj < v) || (vj == v && (pj < p || (pj == p && qj < q)));
         }
         if (lane < NB) { bv[rank] = v; bpq[rank] = p | (q << 8); }
@@ -279,11 +290,14 @@ __device__ void build_table_warp(int n, float a, float b, float *out, float *sm,
         // derivatives n+1..2n+1 of every piece directly (right-sided at its start)
         const float binv = 1.0f / b;
         float am = 1.f;
+#pragma unroll
         for (int k = 0; k < m; ++k) am *= ainv;
         if (lane < nh) {
             const int p0 = mp, q0 = mq;
-            float hi[kMaxM];
+            float hi[n + 1];
+#pragma unroll
             for (int e = 0; e <= n; ++e) hi[e] = 0.f;
+#pragma unroll
             for (int pp = 0; pp <= m; ++pp) {
                 int l;
                 float tau;
@@ -298,13 +312,16 @@ __device__ void build_table_warp(int n, float a, float b, float *out, float *sm,
                     if (l < 0 || l >= m) continue;
                     tau = t - (float)l;
                 }
-                float D[kMaxM];
-                bspline_piece_derivs(n, l, tau, binv, D);
+                float D[n + 1];
+                bspline_piece_derivs<n>(l, tau, binv, D);
                 const float wp = binomf(m, pp) * ((pp & 1) ? -1.f : 1.f);
+#pragma unroll
                 for (int e = 0; e <= n; ++e) hi[e] = __fmaf_rn(wp, D[e], hi[e]);
             }
+#pragma unroll
             for (int e = 0; e <= n; ++e) P[lane * 8 + n + 1 + e] = hi[e] * am / factf(n + 1 + e);
             if (lane == 0)
+#pragma unroll
                 for (int d = 0; d <= n; ++d) P[d] = 0.f;
         }
         __syncwarp();
@@ -314,7 +331,9 @@ __device__ void build_table_warp(int n, float a, float b, float *out, float *sm,
                 const int cur = bpq[pi], prev = bpq[pi - 1];
                 const float dl = sym_diff((cur & 255) - (prev & 255), (cur >> 8) - (prev >> 8), a, b, 0.f);
                 float sacc = 0.f;
-                for (int k = nc - 1; k >= lane; --k) sacc = __fmaf_rn(sacc, dl, binomf(k, lane) * P[(pi - 1) * 8 + k]);
+#pragma unroll
+                for (int k = nc - 1; k >= 0; --k)
+                    if (k >= lane) sacc = __fmaf_rn(sacc, dl, binomf(k, lane) * P[(pi - 1) * 8 + k]);
                 P[pi * 8 + lane] = sacc;
             }
             __syncwarp();
@@ -329,6 +348,7 @@ __device__ void build_table_warp(int n, float a, float b, float *out, float *sm,
             else if (rq > a) { fq += 1; rq = __fmaf_rn((float)(-fq), a, (float)lane * b); }
         }
         int srank = 1;
+#pragma unroll
         for (int j = 1; j <= m; ++j) {
             const float rj = __shfl_sync(0xffffffffu, rq, j);
             srank += (j < lane) ? (rj <= rq) : (j > lane ? (rj < rq) : 0);
@@ -356,10 +376,21 @@ __device__ void build_table_warp(int n, float a, float b, float *out, float *sm,
             const int bp = bpq[pi] & 255, bq = bpq[pi] >> 8;
             const float X = mirror ? sym_diff(m - pl - bp, m - ql - bq, a, b, 0.f) : sym_diff(pl - bp, ql - bq, a, b, 0.f);
             float *T = tab + tab_poly(sg, i);
-            for (int d = 0; d < nc; ++d) {
-                float sacc = 0.f;
-                for (int k = nc - 1; k >= d; --k) sacc = __fmaf_rn(sacc, X, binomf(k, d) * P[pi * 8 + k]);
-                T[2 * d] = (mirror && (d & 1)) ? -sacc : sacc;
+            float c[nc];
+#pragma unroll
+            for (int k = 0; k < nc; ++k) c[k] = P[pi * 8 + k];
+            if (X != 0.f) {
+                // Taylor shift of the piece to the interval start
+#pragma unroll
+                for (int d = 0; d < nc; ++d) {
+                    float sacc = 0.f;
+#pragma unroll
+                    for (int k = nc - 1; k >= d; --k) sacc = __fmaf_rn(sacc, X, binomf(k, d) * c[k]);
+                    T[2 * d] = (mirror && (d & 1)) ? -sacc : sacc;
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < nc; ++d) T[2 * d] = (mirror && (d & 1)) ? -c[d] : c[d];
             }
         }
     }
@@ -370,24 +401,19 @@ __device__ void build_table_warp(int n, float a, float b, float *out, float *sm,
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kTabWarps * 32) tables_kernel(GridDev g, LinesDev L, float *tabs, int64_t n_tab)
+// One warp per table.  a and b were written into the table head by the line
+// setup (FP64 geometry stays there, once per line).
+template <int DEG>
+__global__ void __launch_bounds__(kTabWarps * 32) tables_kernel(float *tabs, int64_t n_tab)
 {
     __shared__ __align__(16) float scratch[kTabWarps][kBuildScratch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * kTabWarps + warp;
     if (t >= n_tab) return;
-    double dx, dy;
-    if (L.kind == SP_LINES_PARALLEL) {
-        double s, c;
-        sincos((double)L.view[t], &s, &c);
-        dx = c; dy = s;
-    } else {
-        double px, py;
-        line_geometry(L, t, dx, dy, px, py);
-    }
-    float af, bf;
-    footprint_ab(g.degree, dx, dy, af, bf);
-    build_table_warp(g.degree, af, bf, tabs + t * (int64_t)kTabFloats, scratch[warp], lane);
+    float *out = tabs + t * (int64_t)kTabFloats;
+    const float af = out[kTabA], bf = out[kTabB];
+    __syncwarp();
+    build_table_warp<DEG>(af, bf, out, scratch[warp], lane);
 }
 
 // ------------------------------------------------------------------ evaluation
@@ -604,7 +630,7 @@ __global__ void footprint_eval_kernel(int64_t count, const float *theta, const f
     sincos((double)theta[r], &s, &c);
     float af, bf;
     footprint_ab(DEG, c, s, af, bf);
-    build_table_warp(DEG, af, bf, nullptr, scratch[warp], lane);
+    build_table_warp<DEG>(af, bf, nullptr, scratch[warp], lane);
     if (lane == 0) out[r] = footprint_from_table<DEG>(scratch[warp], af, bf, yt[r]);
 }
 
@@ -624,21 +650,6 @@ inline unsigned warp_blocks(int64_t lines)
 
 }  // namespace
 
-cudaError_t launch_setup(const GridDev &g, const LinesDev &L, LineHdr *hdr, cudaStream_t s)
-{
-    if (L.m <= 0) return cudaSuccess;
-    setup_kernel<<<blocks_for(L.m, 128), 128, 0, s>>>(g, L, hdr, L.m);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int64_t n_tab,
-                          cudaStream_t s)
-{
-    if (n_tab <= 0) return cudaSuccess;
-    tables_kernel<<<blocks_for(n_tab, kTabWarps), kTabWarps * 32, 0, s>>>(g, L, tabs, n_tab);
-    return cudaGetLastError();
-}
-
 #define SPX_DISPATCH(DEGVAR, KERNEL, GRID, BLOCK, STREAM, ...)                          \
     switch (DEGVAR) {                                                                     \
     case 0: KERNEL<0><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                    \
@@ -646,6 +657,22 @@ cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int6
     case 2: KERNEL<2><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                    \
     default: KERNEL<3><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                   \
     }
+
+cudaError_t launch_setup(const GridDev &g, const LinesDev &L, LineHdr *hdr, float *tabs, cudaStream_t s)
+{
+    if (L.m <= 0) return cudaSuccess;
+    setup_kernel<<<blocks_for(L.m, 128), 128, 0, s>>>(g, L, hdr, tabs, L.m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int64_t n_tab,
+                          cudaStream_t s)
+{
+    (void)L;
+    if (n_tab <= 0) return cudaSuccess;
+    SPX_DISPATCH(g.degree, tables_kernel, blocks_for(n_tab, kTabWarps), kTabWarps * 32, s, tabs, n_tab);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_fwd(const GridDev &g, const LineHdr *hdr, const float *tabs, int64_t m,
                        const float *coef, float *sino, cudaStream_t s)

@@ -85,7 +85,7 @@ sp_status spline_project_fwd_noalloc(const sp_grid *grid, const float *coef, con
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // Records and tables are written whole by the two set-up kernels before
     // the projection reads them, so nothing in the array needs clearing.
-    cudaError_t e = spx::launch_setup(g, L, hdr, s);
+    cudaError_t e = spx::launch_setup(g, L, hdr, tabs, s);
     if (e == cudaSuccess) e = spx::launch_tables(g, L, tabs, n_tab, s);
     if (e == cudaSuccess) e = spx::launch_fwd(g, hdr, tabs, L.m, coef, sino, s);
     if (e != cudaSuccess) return spx::record_error(SP_ECUDA, std::string("forward projection: ") + cudaGetErrorString(e));
