@@ -50,13 +50,11 @@ constexpr int kTabB = 7;                      // head slot of its b
 constexpr int kTabFloats = kTabHead + kMaxSig * kSigStride;   // 328 floats
 constexpr float kBMin = 1e-7f;                // below this b is taken as 0 (Dirac)
 
-// Offset of the polynomial of (interval sg, candidate i) in a table.
-// Candidates are stored in pairs (2p, 2p+1) interleaved coefficient by
-// coefficient, so coefficient d sits at offset + 2 d and a lane that
-// evaluates a pair loads both polynomials as packed pairs.
+// Offset of the polynomial of (interval sg, candidate i) in a table: its
+// kNC coefficients (ascending powers of t) are contiguous, 32-byte aligned.
 __host__ __device__ constexpr int tab_poly(int sg, int i)
 {
-    return kTabHead + sg * kSigStride + (i >> 1) * (2 * kNC) + (i & 1);
+    return kTabHead + sg * kSigStride + i * kNC;
 }
 
 enum LineFlags : int {
@@ -159,14 +157,14 @@ __device__ __forceinline__ U0DF row_start_df(const LineHdr &H, float inv_a, int 
 }
 
 // ------------------------------------------------------------------ row evaluation
-// Horner scheme of a table polynomial (coefficients at stride 2, see tab_poly).
+// Horner scheme of a table polynomial (see tab_poly).
 template <int DEG>
 __device__ __forceinline__ float horner(const float *T, float t)
 {
     constexpr int NC = 2 * DEG + 2;
-    float s = T[2 * (NC - 1)];
+    float s = T[NC - 1];
 #pragma unroll
-    for (int d = NC - 2; d >= 0; --d) s = __fmaf_rn(s, t, T[2 * d]);
+    for (int d = NC - 2; d >= 0; --d) s = __fmaf_rn(s, t, T[d]);
     return s;
 }
 

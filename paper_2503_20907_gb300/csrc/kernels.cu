@@ -258,7 +258,7 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
             const int i = lane / (n + 1), e = lane - i * (n + 1);
             float sc = ainv;
             for (int k = 0; k < e; ++k) sc *= ainv;
-            tab[tab_poly(0, i) + 2 * e] = kBPiece[n][i][e] * sc;
+            tab[tab_poly(0, i) + e] = kBPiece[n][i][e] * sc;
         }
     } else {
         // breakpoints p a + q b, ranked (ties by p, then q)
@@ -386,11 +386,11 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
                     float sacc = 0.f;
 #pragma unroll
                     for (int k = nc - 1; k >= d; --k) sacc = __fmaf_rn(sacc, X, binomf(k, d) * c[k]);
-                    T[2 * d] = (mirror && (d & 1)) ? -sacc : sacc;
+                    T[d] = (mirror && (d & 1)) ? -sacc : sacc;
                 }
             } else {
 #pragma unroll
-                for (int d = 0; d < nc; ++d) T[2 * d] = (mirror && (d & 1)) ? -c[d] : c[d];
+                for (int d = 0; d < nc; ++d) T[d] = (mirror && (d & 1)) ? -c[d] : c[d];
             }
         }
     }

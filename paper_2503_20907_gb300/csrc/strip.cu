@@ -10,11 +10,16 @@
 // Lines whose major axis is x1 use transposed images so that strip rows stay
 // contiguous in global memory.
 //
-// Per line (one warp), a lane takes one major-axis row at a time and all of
-// its candidates, two at a time with packed FP32 FMAs (fma.rn.f32x2): the
-// Horner schemes of a candidate pair advance in one instruction.  The line's
-// footprint table sits in the warp's shared memory; its 16-byte loads are
-// broadcasts, since the lanes of a warp touch at most n+2 of its intervals.
+// One warp takes one line at a time, in batches of up to kBatch rows:
+//   A. lane per row: u_0, its interval sigma, t = u_0 - s_sigma and the strip
+//      offset of the row's first candidate; the rows are then ordered by
+//      sigma (counting sort, in the warp's shared memory);
+//   B. lane per (candidate i, row slot): for each interval sigma the lane
+//      holds the polynomial T[sigma][i] in registers and runs it over the
+//      rows of that interval, two rows per packed FP32 FMA (fma.rn.f32x2).
+// Polynomial coefficients are then read once per interval and batch instead
+// of once per row, which keeps shared-memory traffic to the row records and
+// the coefficients (or strip accumulators) themselves.
 #include <climits>
 
 #include "common.cuh"
@@ -25,20 +30,28 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kChunk = 32;          // lines per chunk
-constexpr int kPitch = 41;          // strip row length (floats); odd, so consecutive rows hit different banks
-constexpr int kSlabRows = 512;      // strip rows held at once
+constexpr int kPitch = 44;          // strip row length (floats), whole 16-byte chunks
+constexpr int kWin = kPitch - 3;    // window width that fits once its start is rounded down to 4 columns
+constexpr int kSlabRows = 408;      // strip rows held at once
+constexpr int kDummy = 16;          // zero floats after the strip: target of padding records
+constexpr int kBatch = 256;         // rows of one line per sorting batch (8 per lane)
+constexpr int kRowsPerLane = kBatch / 32;
+constexpr int kEntCap = kBatch + 4 * kMaxSig;   // sorted row records, segments padded to multiples of 4
 
-constexpr size_t kStripBytes = sizeof(float) * ((kSlabRows * kPitch + 3) & ~3);
+constexpr size_t kStripBytes = sizeof(float) * (kSlabRows * kPitch + kDummy);
 constexpr size_t kCloBytes = sizeof(int) * kSlabRows;
-// Each warp's copy of its current table, interval blocks padded from 64 to 68
-// floats so that the blocks of different intervals start on different banks.
-constexpr int kSigStrideS = kSigStride + 4;
-constexpr int kTabFloatsS = kTabHead + kMaxSig * kSigStrideS;
-constexpr size_t kTabWarpBytes = sizeof(float) * kWarps * kTabFloatsS;
+// Per warp: two table buffers (current line and the next one, loaded
+// asynchronously) and the sorted row records of one batch.
+constexpr size_t kTabBufBytes = sizeof(float) * kTabFloats;
+constexpr size_t kWarpBytes = 2 * kTabBufBytes + 2 * sizeof(float) * kEntCap;   // + t[] and offset[]
 constexpr size_t kAccBytes = sizeof(float) * kChunk;
 constexpr size_t kMiscBytes = 32 + 4 * 64;
 constexpr size_t kHdrBytes = sizeof(LineHdr) * kChunk;
-constexpr size_t kSmemBytes = kStripBytes + kCloBytes + kTabWarpBytes + kAccBytes + kMiscBytes + kHdrBytes;
+constexpr size_t kSmemBytes = kStripBytes + kCloBytes + kWarps * kWarpBytes + kAccBytes + kMiscBytes + kHdrBytes;
+static_assert(kTabBufBytes % 16 == 0 && kWarpBytes % 16 == 0 && kStripBytes % 16 == 0 && kCloBytes % 16 == 0,
+              "16-byte alignment of the shared-memory regions");
+static_assert(kSmemBytes <= 115712, "two CTAs per SM");
+static_assert(kPitch % 4 == 0, "strip rows of whole 16-byte chunks");
 
 // ------------------------------------------------------------------ packed FP32
 typedef unsigned long long f2;
@@ -70,6 +83,16 @@ __device__ __forceinline__ void red_shared(float *p, float v)
 
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 constexpr int kTabLines = (kTabFloats * 4 + 127) / 128;   // 128-byte lines of one table
 
 // First and last column of the run of line H in row r, for a run of K nodes.
@@ -84,88 +107,160 @@ __device__ __forceinline__ void run_columns(const LineHdr &H, float inv_a, int r
     hi = max(q0, q1);
 }
 
-// One line over the strip rows [S0, S1).  Forward (ADJ false): returns
-// sum_k c_k phi (no factor h).  Adjoint: adds hp * phi into the strip.
-//
-// Lane l takes rows S0' + l, S0' + l + 32, ...  The line's footprint table
-// has been copied to this warp's shared memory (tabw); a row in interval
-// sigma evaluates candidate pair p with the packed polynomials at
-// tab_poly(sigma, 2p).  Lanes of one warp touch at most n+2 different
-// intervals, so each 16-byte table load is a broadcast of few addresses.
+// Copy one footprint table (kTabFloats floats, 16-byte chunks) to shared memory.
+__device__ __forceinline__ void table_copy_async(float *dst, const float *src, int lane)
+{
+    for (int i = lane; i < kTabFloats / 4; i += 32) cp_async16(dst + 4 * i, src + 4 * i);
+}
+
+// One line over the strip rows [S0, S1).  Forward (ADJ false): returns this
+// lane's part of sum_k c_k phi (no factor h).  Adjoint: adds hp * phi into the
+// strip.  tabw is the line's table in shared memory; ent_t / ent_p hold the
+// warp's sorted row records (t, strip offset of candidate 0).
 template <int DEG, bool ADJ>
-__device__ float strip_line(const LineHdr &H, const float *tabw, const float *__restrict__ tab, float *strip,
-                            const int *clo, int S0, int S1, int lane, const float *__restrict__ src,
-                            float *dst, int Nq, int *err, float hp)
+__device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, int *ent_p, float *strip, const int *clo,
+                            int S0, int S1, int lane, const float *__restrict__ src, float *dst, int Nq,
+                            int *err, float hp)
 {
     constexpr int NC = 2 * DEG + 2;
+    constexpr int NS = DEG + 2;       // intervals sigma
     const int sgn = (H.flags & kKapNeg) ? -1 : 1;
     const float inv_a = 1.0f / H.a;
     float s[DEG + 1];
 #pragma unroll
     for (int q = 0; q <= DEG; ++q) s[q] = tabw[q];
     const int K = H.K;
-    const int np = (K + 1) >> 1;
-    const bool odd = K & 1;
-    f2 acc2 = 0ull, acc2b = 0ull;
+    // phase B lane roles: candidate ci of row slot sl (nsl slots of K lanes)
+    const int rk = (256 + K - 1) / K;   // (l * rk) >> 8 == l / K for l < 32, K <= 8
+    const int nsl = (32 * rk) >> 8;
+    const int sl = (lane * rk) >> 8;
+    const int ci = lane - sl * K;
+    const bool lane_on = sl < nsl;
+    const int coloff = sgn * ci;
+    f2 acc2 = 0ull;
     float acc_slow = 0.f;
 
+    const int dummy_pos = kSlabRows * kPitch + kDummy / 2;
     const int rb = max(H.r_begin, S0), re = min(H.r_end, S1);
-    for (int r = rb + lane; r < re; r += 32) {
-        const RowEval e = row_eval<DEG>(H, s, inv_a, sgn, r);
-        const int rr = r - S0;
-        const int oq = e.q0 - clo[rr];
-        const int lo = sgn > 0 ? oq : oq - (K - 1);
-        const int hi = sgn > 0 ? oq + (K - 1) : oq;
-        if (lo >= 0 && hi < kPitch) {
-            const float *row = strip + rr * kPitch + oq;
-            const f2 tt = f2pack(e.t, e.t);
-            const float *T = tabw + kTabHead + e.sg * kSigStrideS;
-            for (int p = 0; p < np; ++p) {
-                const ulonglong2 *tp = reinterpret_cast<const ulonglong2 *>(T + p * 2 * kNC);
-                f2 Tp[NC];
+    for (int r0 = rb; r0 < re; r0 += kBatch) {
+        // ---- A: lane per row
+        float tv[kRowsPerLane];
+        int pv[kRowsPerLane], sv[kRowsPerLane];
+        unsigned long long own = 0ull;
 #pragma unroll
-                for (int v = 0; v < NC / 2; ++v) {
-                    const ulonglong2 x = tp[v];
-                    Tp[2 * v] = x.x;
-                    Tp[2 * v + 1] = x.y;
-                }
-                f2 ph = Tp[NC - 1];
-#pragma unroll
-                for (int d = NC - 2; d >= 0; --d) ph = f2fma(ph, tt, Tp[d]);
-                const bool has_b = !(odd && p == np - 1);
-                const int ia = sgn * 2 * p;
-                if constexpr (ADJ) {
-                    float pa, pb;
-                    f2unpack(ph, pa, pb);
-                    red_shared(const_cast<float *>(row) + ia, hp * pa);
-                    if (has_b) red_shared(const_cast<float *>(row) + ia + sgn, hp * pb);
+        for (int j = 0; j < kRowsPerLane; ++j) {
+            const int r = r0 + j * 32 + lane;
+            sv[j] = -1;
+            tv[j] = 0.f;
+            pv[j] = 0;
+            if (r < re) {
+                const RowEval e = row_eval<DEG>(H, s, inv_a, sgn, r);
+                const int rr = r - S0;
+                const int oq = e.q0 - clo[rr];
+                const int lo = sgn > 0 ? oq : oq - (K - 1);
+                const int hi = sgn > 0 ? oq + (K - 1) : oq;
+                if (lo >= 0 && hi < kPitch) {
+                    sv[j] = e.sg;
+                    tv[j] = e.t;
+                    pv[j] = rr * kPitch + oq;
+                    own += 1ull << (9 * e.sg);
                 } else {
-                    const float ca = row[ia];
-                    const float cb = has_b ? row[ia + sgn] : 0.f;
-                    if (p & 1) acc2b = f2fma(f2pack(ca, cb), ph, acc2b);
-                    else acc2 = f2fma(f2pack(ca, cb), ph, acc2);
-                }
-            }
-        } else {
-            // run outside the staged window: straight from or to global memory
-            atomicAdd(err, 1);
-            for (int i = 0; i < K; ++i) {
-                const int q = e.q0 + sgn * i;
-                if ((unsigned)q < (unsigned)Nq) {
-                    const float phi = horner<DEG>(tab + tab_poly(e.sg, i), e.t);
-                    if constexpr (ADJ) atomicAdd(dst + (size_t)r * Nq + q, hp * phi);
-                    else acc_slow = __fmaf_rn(__ldg(src + (size_t)r * Nq + q), phi, acc_slow);
+                    // run outside the staged window: straight from or to global memory
+                    atomicAdd(err, 1);
+                    const float *T0 = tabw + tab_poly(e.sg, 0);
+                    for (int i = 0; i < K; ++i) {
+                        const int q = e.q0 + sgn * i;
+                        if ((unsigned)q < (unsigned)Nq) {
+                            const float phi = horner<DEG>(T0 + i * kNC, e.t);
+                            if constexpr (ADJ) atomicAdd(dst + (size_t)r * Nq + q, hp * phi);
+                            else acc_slow = __fmaf_rn(__ldg(src + (size_t)r * Nq + q), phi, acc_slow);
+                        }
+                    }
                 }
             }
         }
+        // counting sort by sigma: 9-bit counters per interval, packed
+        unsigned long long inc = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const unsigned long long tot = __shfl_sync(0xffffffffu, inc, 31);
+        int segb[NS], segn[NS];   // segment start and padded length (a multiple of 4)
+        unsigned long long basep = 0ull;
+        {
+            int b = 0;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const int c = (int)((tot >> (9 * q)) & 511ull);
+                const int cp = (c + 3) & ~3;
+                segb[q] = b;
+                segn[q] = cp;
+                basep |= (unsigned long long)b << (9 * q);
+                // padding records (t = 0, zero target) complete the segment
+                if (lane < cp - c) { ent_t[b + c + lane] = 0.f; ent_p[b + c + lane] = dummy_pos; }
+                b += cp;
+            }
+        }
+        unsigned long long cur = basep + (inc - own);
+#pragma unroll
+        for (int j = 0; j < kRowsPerLane; ++j) {
+            if (sv[j] >= 0) {
+                const int sh = 9 * sv[j];
+                const int idx = (int)((cur >> sh) & 511ull);
+                cur += 1ull << sh;
+                ent_t[idx] = tv[j];
+                ent_p[idx] = pv[j];
+            }
+        }
+        __syncwarp();
+        // ---- B: lane per (candidate, row slot), four rows per step
+        if (lane_on) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const int n = segn[q];
+                if (n == 0) continue;
+                const float *Tq = tabw + tab_poly(q, ci);
+                f2 C[NC];
+#pragma unroll
+                for (int d = 0; d < NC; ++d) {
+                    const float c = ADJ ? Tq[d] * hp : Tq[d];
+                    C[d] = f2pack(c, c);
+                }
+                const int end = segb[q] + n;
+                for (int e = segb[q] + 4 * sl; e < end; e += 4 * nsl) {
+                    const ulonglong2 tt = *reinterpret_cast<const ulonglong2 *>(ent_t + e);
+                    const int4 P = *reinterpret_cast<const int4 *>(ent_p + e);
+                    f2 pa = C[NC - 1], pb = C[NC - 1];
+#pragma unroll
+                    for (int d = NC - 2; d >= 0; --d) {
+                        pa = f2fma(pa, tt.x, C[d]);
+                        pb = f2fma(pb, tt.y, C[d]);
+                    }
+                    if constexpr (ADJ) {
+                        float f0, f1, f2_, f3;
+                        f2unpack(pa, f0, f1);
+                        f2unpack(pb, f2_, f3);
+                        red_shared(strip + P.x + coloff, f0);
+                        red_shared(strip + P.y + coloff, f1);
+                        red_shared(strip + P.z + coloff, f2_);
+                        red_shared(strip + P.w + coloff, f3);
+                    } else {
+                        acc2 = f2fma(f2pack(strip[P.x + coloff], strip[P.y + coloff]), pa, acc2);
+                        acc2 = f2fma(f2pack(strip[P.z + coloff], strip[P.w + coloff]), pb, acc2);
+                    }
+                }
+            }
+        }
+        __syncwarp();
     }
     if constexpr (ADJ) {
         return 0.f;
     } else {
-        float a0, a1, b0, b1;
+        float a0, a1;
         f2unpack(acc2, a0, a1);
-        f2unpack(acc2b, b0, b1);
-        return warp_sum((a0 + a1) + (b0 + b1) + acc_slow);
+        return (a0 + a1) + acc_slow;
     }
 }
 
@@ -176,15 +271,15 @@ template <int DEG, bool ADJ>
 __global__ void __launch_bounds__(kThreads, 2)
 strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
              const float *__restrict__ coef, const float *__restrict__ coefT, float *__restrict__ sino,
-             float *__restrict__ out, float *__restrict__ outT, int chunks_per_view, int *err)
+             float *__restrict__ out, float *__restrict__ outT, int chunks_per_view, int vec, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     float *strip = reinterpret_cast<float *>(smem);
     size_t o = kStripBytes;
     int *clo = reinterpret_cast<int *>(smem + o);
     o += kCloBytes;
-    float *tabw_all = reinterpret_cast<float *>(smem + o);
-    o += kTabWarpBytes;
+    unsigned char *warp_area = smem + o;
+    o += kWarps * kWarpBytes;
     float *line_acc = reinterpret_cast<float *>(smem + o);
     o += kAccBytes;
     int *misc = reinterpret_cast<int *>(smem + o);
@@ -193,13 +288,16 @@ strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float
     LineHdr *hdr_s = reinterpret_cast<LineHdr *>(smem + o);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *tabw = tabw_all + warp * kTabFloatsS;
+    float *tabbuf = reinterpret_cast<float *>(warp_area + warp * kWarpBytes);   // [2][kTabFloats]
+    float *ent_t = reinterpret_cast<float *>(warp_area + warp * kWarpBytes + 2 * kTabBufBytes);
+    int *ent_p = reinterpret_cast<int *>(ent_t + kEntCap);
     const int v = blockIdx.x / chunks_per_view, cb = blockIdx.x - v * chunks_per_view;
     const int j0 = cb * kChunk;
     const int nl = min(kChunk, L.n_det - j0);
     const int64_t line0 = (int64_t)v * L.n_det + j0;
 
     if (!ADJ && threadIdx.x < kChunk) line_acc[threadIdx.x] = 0.f;
+    if (!ADJ && threadIdx.x < kDummy) strip[kSlabRows * kPitch + threadIdx.x] = 0.f;
     // the chunk's line records into shared memory, its tables towards L2
     for (int i = threadIdx.x; i < nl * 4; i += kThreads)
         reinterpret_cast<int4 *>(hdr_s)[i] = __ldg(reinterpret_cast<const int4 *>(hdr + line0) + i);
@@ -266,7 +364,7 @@ strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float
                 wmax = max(wmax, max(hi1, hi2) - min(lo1, lo2) + 5);
             }
             __syncthreads();
-            if (wmax > kPitch && first < last) {
+            if (wmax > kWin && first < last) {
                 if (threadIdx.x == 0) {
                     const int mid = (first + last) >> 1;
                     const int s2 = misc[3];
@@ -287,55 +385,97 @@ strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float
                     run_columns(Hf, inv_af, S0 + rr, lo1, hi1);
                     run_columns(Hl, inv_al, S0 + rr, lo2, hi2);
                     const int lo = min(lo1, lo2) - 2, hi = max(hi1, hi2) + 2;
-                    clo[rr] = lo - max(0, (kPitch - (hi - lo + 1)) / 2);
+                    // centred in the usable width, start rounded down to a 16-byte chunk
+                    clo[rr] = (lo - max(0, (kWin - (hi - lo + 1)) / 2)) & ~3;
                 }
                 __syncthreads();
+                constexpr int kCh = kPitch / 4;   // 16-byte chunks per strip row
                 if constexpr (ADJ) {
-                    for (int i = threadIdx.x; i < nrows * kPitch; i += kThreads) strip[i] = 0.f;
+                    float4 *s4 = reinterpret_cast<float4 *>(strip);
+                    for (int i = threadIdx.x; i < nrows * kCh; i += kThreads) s4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else if (vec) {
+                    // asynchronous 16-byte copies; chunks are wholly inside or
+                    // outside the grid (Nq and chunk starts are multiples of 4)
+                    for (int i = threadIdx.x; i < nrows * kCh; i += kThreads) {
+                        const int rr = i / kCh, cc = i - rr * kCh;
+                        const int q = clo[rr] + 4 * cc;
+                        const bool in = (unsigned)q < (unsigned)Nq;
+                        const float *gp = in ? src + (size_t)(S0 + rr) * Nq + q : src;
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                                         (unsigned)__cvta_generic_to_shared(strip + 4 * i)),
+                                     "l"(gp), "r"(in ? 16 : 0)
+                                     : "memory");
+                    }
+                    asm volatile("cp.async.wait_all;" ::: "memory");
                 } else {
-                    // asynchronous copies, zero-filled outside the grid; one wait
-                    for (int rr = warp; rr < nrows; rr += kWarps) {
-                        const int c0 = clo[rr];
-                        const float *row = src + (size_t)(S0 + rr) * Nq;
-                        for (int cc = lane; cc < kPitch; cc += 32) {
-                            const int q = c0 + cc;
-                            const bool in = (unsigned)q < (unsigned)Nq;
-                            const unsigned dsts = (unsigned)__cvta_generic_to_shared(strip + rr * kPitch + cc);
-                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dsts),
-                                         "l"(in ? row + q : src), "r"(in ? 4 : 0)
-                                         : "memory");
-                        }
+                    // 4-byte copies, zero-filled outside the grid
+                    for (int i = threadIdx.x; i < nrows * kPitch; i += kThreads) {
+                        const int rr = i / kPitch, cc = i - rr * kPitch;
+                        const int q = clo[rr] + cc;
+                        const bool in = (unsigned)q < (unsigned)Nq;
+                        const float *gp = in ? src + (size_t)(S0 + rr) * Nq + q : src;
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                                         (unsigned)__cvta_generic_to_shared(strip + i)),
+                                     "l"(gp), "r"(in ? 4 : 0)
+                                     : "memory");
                     }
                     asm volatile("cp.async.wait_all;" ::: "memory");
                 }
                 __syncthreads();
-                for (int li = first + warp; li <= last; li += kWarps) {
-                    if (!((gmask >> li) & 1u)) continue;
-                    const LineHdr H = hdr_s[li];
-                    const float *tab = tabs + (int64_t)H.tab * kTabFloats;
-                    const float hp = ADJ ? g.h * sino[line0 + li] : 0.f;
+                // this warp's lines of the group: li = first + warp + k kWarps in gmask;
+                // the table of the next one is loaded while the current one runs
+                int li = first + warp;
+                while (li <= last && !((gmask >> li) & 1u)) li += kWarps;
+                int buf = 0;
+                if (li <= last) {
+                    table_copy_async(tabbuf, tabs + (int64_t)hdr_s[li].tab * kTabFloats, lane);
+                    cp_async_commit();
+                }
+                while (li <= last) {
+                    int ln = li + kWarps;
+                    while (ln <= last && !((gmask >> ln) & 1u)) ln += kWarps;
+                    if (ln <= last)
+                        table_copy_async(tabbuf + (buf ^ 1) * kTabFloats,
+                                         tabs + (int64_t)hdr_s[ln].tab * kTabFloats, lane);
+                    cp_async_commit();
+                    cp_async_wait<1>();
                     __syncwarp();
-                    for (int i = lane; i < kTabFloats / 4; i += 32) {
-                        // head (2 float4), then 16 float4 per interval block
-                        const int blk = i < 2 ? -1 : (i - 2) >> 4;
-                        const int dst4 = i < 2 ? i : 2 + blk * (kSigStrideS / 4) + ((i - 2) & 15);
-                        reinterpret_cast<float4 *>(tabw)[dst4] = __ldg(reinterpret_cast<const float4 *>(tab) + i);
+                    const LineHdr H = hdr_s[li];
+                    const float hp = ADJ ? g.h * sino[line0 + li] : 0.f;
+                    const float part = strip_line<DEG, ADJ>(H, tabbuf + buf * kTabFloats, ent_t, ent_p, strip, clo, S0, S1,
+                                                            lane, src, dst, Nq, err, hp);
+                    if (!ADJ) {
+                        const float sum = warp_sum(part);
+                        if (lane == 0) line_acc[li] += sum;
                     }
                     __syncwarp();
-                    const float sum = strip_line<DEG, ADJ>(H, tabw, tab, strip, clo, S0, S1, lane, src, dst, Nq,
-                                                           err, hp);
-                    if (!ADJ && lane == 0) line_acc[li] += sum;
+                    li = ln;
+                    buf ^= 1;
                 }
+                cp_async_wait<0>();
                 if constexpr (ADJ) {
                     __syncthreads();
-                    // add the accumulated strip into the image, row by row
-                    for (int rr = warp; rr < nrows; rr += kWarps) {
-                        const int c0 = clo[rr];
-                        float *row = dst + (size_t)(S0 + rr) * Nq;
-                        for (int cc = lane; cc < kPitch; cc += 32) {
-                            const int q = c0 + cc;
-                            const float val = strip[rr * kPitch + cc];
-                            if ((unsigned)q < (unsigned)Nq && val != 0.f) atomicAdd(row + q, val);
+                    // add the accumulated strip into the image
+                    if (vec) {
+                        const float4 *s4 = reinterpret_cast<const float4 *>(strip);
+                        for (int i = threadIdx.x; i < nrows * kCh; i += kThreads) {
+                            const int rr = i / kCh, cc = i - rr * kCh;
+                            const int q = clo[rr] + 4 * cc;
+                            const float4 v4 = s4[i];
+                            if ((unsigned)q < (unsigned)Nq &&
+                                (v4.x != 0.f || v4.y != 0.f || v4.z != 0.f || v4.w != 0.f))
+                                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(
+                                                 dst + (size_t)(S0 + rr) * Nq + q),
+                                             "f"(v4.x), "f"(v4.y), "f"(v4.z), "f"(v4.w)
+                                             : "memory");
+                        }
+                    } else {
+                        for (int i = threadIdx.x; i < nrows * kPitch; i += kThreads) {
+                            const int rr = i / kPitch, cc = i - rr * kPitch;
+                            const int q = clo[rr] + cc;
+                            const float val = strip[i];
+                            if ((unsigned)q < (unsigned)Nq && val != 0.f)
+                                atomicAdd(dst + (size_t)(S0 + rr) * Nq + q, val);
                         }
                     }
                 }
@@ -396,8 +536,12 @@ cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *h
     if (e != cudaSuccess) return e;
     const int cpv = (L.n_det + kChunk - 1) / kChunk;
     const unsigned grid = (unsigned)(L.n_view * cpv);
+    // 16-byte staging and flushing: image rows (nx and ny floats) and bases aligned
+    const float *img = ADJ ? out : coef;
+    const int vec = (g.nx % 4 == 0) && (g.ny % 4 == 0) && ((reinterpret_cast<uintptr_t>(img) & 15) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(imgT) & 15) == 0);
     strip_kernel<DEG, ADJ><<<grid, kThreads, kSmemBytes, s>>>(g, L, hdr, tabs, coef, imgT,
-                                                              const_cast<float *>(sino), out, imgT, cpv, err);
+                                                              const_cast<float *>(sino), out, imgT, cpv, vec, err);
     e = cudaGetLastError();
     if (e == cudaSuccess && ADJ) {
         add_transposed_kernel<<<tg, tb, 0, s>>>(imgT, out, g.nx, g.ny);
