@@ -34,6 +34,8 @@ METRIC = "Mrays/s fwd+adj at 512² cubic fan-beam (% roofline); learned-vs-cold 
 UNIT = "Mrays/s"
 WORKLOAD = "fan512_cubic"
 FP32_LANES_PER_SM = 128
+KERNELS_PER_STEP = 6   # line setup, tables, transpose + forward strip, adjoint strip + transposed add
+CG_ITERS = 100
 FLOPS_PER_PAIR = lambda n: 2 * (2 * n + 3)   # noqa: E731  (2n+1 Horner FMAs, 1 offset, 1 accumulate)
 
 
@@ -44,6 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cg", action="store_true", help="skip the CGLS timing (not part of the step)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="fan512_cubic (the benchmark) or fan256_cubic (small profiling case)")
     return ap.parse_args()
@@ -268,6 +271,27 @@ def run_ours(args, rank, ws, local):
     h2d = coef_h.numel() * 4 + view_h.numel() * 4
     d2h = sino_h.numel() * 4 + back_h.numel() * 4
 
+    # CGLS on transmission data of the same scan (the reconstruction step)
+    cg = None
+    if not args.no_cg:
+        plan.fwd(coef, sino, stream)
+        b_np, _ = workloads.transmission_data(sino.cpu().numpy(), seed=3)
+        b_cg = torch.from_numpy(b_np.astype(np.float32)).to(dev)
+        plan.cgls(b_cg, 2)                       # allocates the plan's CG workspace
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, gam = plan.cgls(b_cg, CG_ITERS)
+        b.record(stream)
+        b.synchronize()
+        g = gam.cpu().numpy()
+        cg = {"workload": f"{wl.name} transmission data (peak attenuation 3, I0 1e4, Poisson seed 3), x0 = 0",
+              "iters": CG_ITERS, "ms_per_iter": a.elapsed_time(b) / CG_ITERS,
+              "rel_residual_normal_eq": float(np.sqrt(g[-1] / g[0])),
+              "first_iter_rel_residual_below_1e-4": next((k for k in range(len(g)) if np.sqrt(g[k] / g[0]) < 1e-4),
+                                                         None),
+              "kernels_per_iter": 8}
+
     if rank != 0:
         return
     value = ws * M * args.steps / tmax / 1e6
@@ -297,10 +321,12 @@ def run_ours(args, rank, ws, local):
                      "flops_per_pair": FLOPS_PER_PAIR(wl.degree)},
         "e2e": {"value": M * args.steps / e2e_t / 1e6 * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
         "wall_s": wall,
     }
+    if cg is not None:
+        line["cg"] = cg
     if ws == 1 and not args.no_cpu_baseline and wl.name == WORKLOAD:
         cb = oracle_sample(wl)
         cb.pop("seconds", None)

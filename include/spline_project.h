@@ -165,6 +165,31 @@ sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan
 sp_status spline_plan_prepare(sp_plan *plan, void *stream);
 sp_status spline_plan_fwd(const sp_plan *plan, const float *coef, float *sino, void *stream);
 sp_status spline_plan_adj(const sp_plan *plan, const float *sino, float *coef_out, void *stream);
+/*
+ * Least squares with the plan's projector A: conjugate gradients on the
+ * normal equations A^T A x = A^T b (CGLS), the reconstruction step of Sec. V,
+ * where the system is solved by conjugate gradients.  With x_0 the initial x:
+ *   r = b - A x_0;  s = A^T r;  p = s;  gamma = <s, s>
+ *   for k = 1..iters:
+ *     q = A p;  alpha = gamma / <q, q>;  x += alpha p;  r -= alpha q;
+ *     s = A^T r;  gamma' = <s, s>;  p = s + (gamma' / gamma) p;  gamma = gamma'.
+ * x_k minimises ||b - A x|| over x_0 + span{A^T r_0, (A^T A) A^T r_0, ...}.
+ *   b           device float32 [m], the data (not modified).
+ *   x           device float32 [ny][nx]: x_0 on entry, x_iters on return.
+ *               Must not overlap b.
+ *   iters       number of iterations, >= 0 (0 only evaluates gamma_0).
+ *   gamma_hist  NULL, or device double [iters + 1]: gamma_k =
+ *               ||A^T (b - A x_k)||^2 for k = 0..iters; the relative residual
+ *               of the normal equations is sqrt(gamma_k / gamma_0).
+ * Vectors are FP32; dot products accumulate in FP64 with a fixed summation
+ * order (results are reproducible run to run).  A step whose <q, q> or gamma
+ * is 0 leaves x unchanged.  Scalars stay on the device: the call enqueues the
+ * whole solve on `stream` without waiting.  Workspace (2 m + 2 ny nx floats)
+ * is allocated in the plan on first use (cudaMalloc, which synchronises the
+ * device) and freed with the plan.
+ */
+sp_status spline_plan_cgls(sp_plan *plan, const float *b, float *x, int32_t iters,
+                           double *gamma_hist, void *stream);
 /* Number of lines of the plan (-1 if plan is NULL). */
 int64_t spline_plan_lines(const sp_plan *plan);
 /*

@@ -9,7 +9,9 @@ the C ABI of include/spline_project.h; this package is a thin ctypes binding
 from ._lib import (Grid, Lines, Plan, SplineError, load, sp_release_workspace, sp_version,
                    spline_footprint_eval, spline_lines_expand, spline_project_adj,
                    spline_project_fwd, spline_visited)
+from .autograd import backproject, project
 
-__all__ = ["Grid", "Lines", "Plan", "SplineError", "load", "sp_release_workspace", "sp_version",
+__all__ = ["Grid", "Lines", "Plan", "SplineError", "backproject", "load", "project",
+           "sp_release_workspace", "sp_version",
            "spline_footprint_eval", "spline_lines_expand", "spline_project_adj",
            "spline_project_fwd", "spline_visited"]

@@ -44,7 +44,7 @@ EXPORTED = ("sp_lines_count", "spline_project_fwd", "spline_project_adj", "splin
             "spline_footprint_eval", "spline_visited", "sp_release_workspace", "sp_last_error",
             "sp_version", "spline_plan_create", "spline_plan_prepare", "spline_plan_fwd",
             "spline_plan_adj", "spline_plan_lines", "spline_plan_destroy", "spline_plan_stats",
-            "spline_project_fwd_noalloc")
+            "spline_project_fwd_noalloc", "spline_plan_cgls")
 
 
 def load(build_if_stale: bool = True) -> ctypes.CDLL:
@@ -82,6 +82,8 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
     lib.spline_plan_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.spline_project_fwd_noalloc.restype = st
     lib.spline_project_fwd_noalloc.argtypes = [G, P, L, P, P]
+    lib.spline_plan_cgls.restype = st
+    lib.spline_plan_cgls.argtypes = [P, P, P, ctypes.c_int32, P, P]
     lib.spline_plan_destroy.restype = st
     lib.spline_plan_destroy.argtypes = [P]
     lib.sp_release_workspace.restype = st
@@ -284,6 +286,25 @@ class Plan:
             raise ValueError("coef_out must be a contiguous tensor of ny*nx values")
         _check(load().spline_plan_adj(self._h, p.data_ptr(), coef_out.data_ptr(), _stream(stream)))
         return coef_out
+
+    def cgls(self, b: torch.Tensor, iters: int, x0: torch.Tensor | None = None,
+             history: bool = True, stream=None):
+        """Least squares min ||A x - b|| by CGLS (spline_plan_cgls).
+
+        Returns (x, gamma) with x the last iterate [ny][nx] and gamma the FP64
+        history ||A^T (b - A x_k)||^2, k = 0..iters (None if history is False).
+        x0 (default zeros) is not modified."""
+        bb = _dev_f32(b, "b")
+        if bb.numel() != self.m:
+            raise ValueError("b must hold m values")
+        if x0 is None:
+            x = torch.zeros(self.grid.ny, self.grid.nx, dtype=torch.float32, device=bb.device)
+        else:
+            x = _dev_f32(x0, "x0").clone().reshape(self.grid.ny, self.grid.nx)
+        gam = torch.empty(iters + 1, dtype=torch.float64, device=bb.device) if history else None
+        _check(load().spline_plan_cgls(self._h, bb.data_ptr(), x.data_ptr(), int(iters),
+                                       gam.data_ptr() if history else None, _stream(stream)))
+        return x, gam
 
     def slow_rows(self) -> int:
         """Rows read from global memory because they fell outside the staged window."""

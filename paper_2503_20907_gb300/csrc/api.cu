@@ -300,6 +300,8 @@ struct sp_plan {
     float *tabs;
     void *extra;       // strip scratch (transposed coefficients, slow-row counter) or NULL
     bool prepared;
+    void *cg_ws;       // CGLS vectors and scalars, allocated on first use
+    size_t cg_bytes;
 };
 
 sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan **plan)
@@ -335,6 +337,8 @@ sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan
     p->tabs = mem ? reinterpret_cast<float *>(static_cast<char *>(mem) + hb) : nullptr;
     p->extra = (mem && xb) ? static_cast<char *>(mem) + hb + tb : nullptr;
     p->prepared = false;
+    p->cg_ws = nullptr;
+    p->cg_bytes = 0;
     if (p->extra) {
         e = cudaMemset(slow_counter(g, p->extra), 0, sizeof(int));
         if (e != cudaSuccess) {
@@ -385,6 +389,51 @@ sp_status spline_plan_adj(const sp_plan *plan, const float *sino, float *coef_ou
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "adjoint projection");
 }
 
+namespace {
+cudaError_t plan_fwd_cb(void *ctx, const float *coef, float *sino, cudaStream_t s)
+{
+    const sp_plan *p = static_cast<const sp_plan *>(ctx);
+    return run_fwd(p->g, p->L, p->hdr, p->tabs, p->extra, coef, sino, s);
+}
+cudaError_t plan_adj_cb(void *ctx, const float *sino, float *coef_out, cudaStream_t s)
+{
+    const sp_plan *p = static_cast<const sp_plan *>(ctx);
+    return run_adj(p->g, p->L, p->hdr, p->tabs, p->extra, sino, coef_out, s);
+}
+}  // namespace
+
+sp_status spline_plan_cgls(sp_plan *plan, const float *b, float *x, int32_t iters, double *gamma_hist,
+                           void *stream)
+{
+    g_err.clear();
+    if (!plan) return fail(SP_EINVAL, "plan is NULL");
+    if (!plan->prepared) return fail(SP_EINVAL, "plan not prepared");
+    if (!x) return fail(SP_EINVAL, "x pointer is NULL");
+    if (plan->L.m > 0 && !b) return fail(SP_EINVAL, "b pointer is NULL");
+    if (iters < 0) return fail(SP_EINVAL, "iters must be >= 0");
+    const int64_t n = (int64_t)plan->g.nx * plan->g.ny, m = plan->L.m;
+    const size_t need = spx::cg_workspace_bytes(n, m);
+    if (plan->cg_bytes < need) {
+        if (plan->cg_ws) {
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            cudaFree(plan->cg_ws);
+            plan->cg_ws = nullptr;
+            plan->cg_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&plan->cg_ws, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            plan->cg_ws = nullptr;
+            return fail(SP_ENOMEM, std::string("CGLS workspace allocation failed: ") + cudaGetErrorString(e));
+        }
+        plan->cg_bytes = need;
+    }
+    spx::CgOps ops{plan, plan_fwd_cb, plan_adj_cb};
+    cudaError_t e = spx::run_cgls(ops, n, m, b, x, iters, gamma_hist, plan->cg_ws, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SP_OK : cuda_fail(e, "CGLS");
+}
+
 int64_t spline_plan_lines(const sp_plan *plan) { return plan ? plan->L.m : -1; }
 
 sp_status spline_plan_stats(const sp_plan *plan, int64_t *slow_rows)
@@ -405,10 +454,11 @@ sp_status spline_plan_destroy(sp_plan *plan)
     g_err.clear();
     if (!plan) return SP_OK;
     sp_status st = SP_OK;
-    if (plan->mem) {
+    if (plan->mem || plan->cg_ws) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) st = cuda_fail(e, "cudaDeviceSynchronize");
-        cudaFree(plan->mem);
+        if (plan->mem) cudaFree(plan->mem);
+        if (plan->cg_ws) cudaFree(plan->cg_ws);
     }
     delete plan;
     return st;

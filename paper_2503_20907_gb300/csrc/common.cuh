@@ -250,4 +250,16 @@ cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr 
 cudaError_t launch_footprint_eval(int degree, int64_t count, const float *theta, const float *yt,
                                   float *out, float *scratch, cudaStream_t s);
 
+
+// CGLS (cg.cu).  The projector is passed as callbacks so that cg.cu does not
+// depend on how a plan runs its projections.
+struct CgOps {
+    void *ctx;
+    cudaError_t (*fwd)(void *ctx, const float *coef, float *sino, cudaStream_t s);
+    cudaError_t (*adj)(void *ctx, const float *sino, float *coef_out, cudaStream_t s);
+};
+size_t cg_workspace_bytes(int64_t n, int64_t m);
+cudaError_t run_cgls(const CgOps &ops, int64_t n, int64_t m, const float *b, float *x, int iters, double *hist,
+                     void *ws, cudaStream_t s);
+
 }  // namespace spx

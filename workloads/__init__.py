@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "ellipse_phantom", "Geometry", "Workload", "workload", "crop_workload",
-    "random_lines_circle", "poisson_counts",
+    "random_lines_circle", "poisson_counts", "transmission_data",
 ]
 
 
@@ -173,3 +173,17 @@ def poisson_counts(expected: np.ndarray, seed: int) -> np.ndarray:
     """Poisson draws with the given means (float64 in, float64 out)."""
     rng = np.random.default_rng(seed)
     return rng.poisson(np.asarray(expected, dtype=np.float64)).astype(np.float64)
+
+
+def transmission_data(expected: np.ndarray, seed: int, peak: float = 3.0, I0: float = 1e4):
+    """Noisy line integrals for a transmission scan of a noiseless sinogram.
+
+    Scale kappa = peak / max(expected) (so the largest attenuation is
+    ``peak``); counts ~ Poisson(I0 exp(-kappa expected)); returned data
+    -ln(max(counts, 1) / I0) / kappa (float64), in the units of ``expected``,
+    and kappa."""
+    e = np.asarray(expected, dtype=np.float64)
+    top = float(e.max())
+    kappa = peak / top if top > 0 else 1.0
+    counts = poisson_counts(I0 * np.exp(-kappa * e), seed)
+    return -np.log(np.maximum(counts, 1.0) / I0) / kappa, kappa
