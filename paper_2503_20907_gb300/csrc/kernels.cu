@@ -24,14 +24,15 @@ __device__ const float kBPiece[4][4][4] = {
      {1.f / 6.f, -0.5f, 0.5f, -1.f / 6.f}},
 };
 
-// Binomial coefficients C(k, d), k, d < 8 (Pascal's triangle).
-__constant__ float kBinom[8][8] = {
-    {1, 0, 0, 0, 0, 0, 0, 0},      {1, 1, 0, 0, 0, 0, 0, 0},       {1, 2, 1, 0, 0, 0, 0, 0},
-    {1, 3, 3, 1, 0, 0, 0, 0},      {1, 4, 6, 4, 1, 0, 0, 0},       {1, 5, 10, 10, 5, 1, 0, 0},
-    {1, 6, 15, 20, 15, 6, 1, 0},   {1, 7, 21, 35, 35, 21, 7, 1},
-};
-
-__device__ __forceinline__ float binomf(int n, int k) { return kBinom[n][k]; }
+// Binomial coefficient C(n, k) (exact in float for n < 25); folded to a
+// constant wherever its arguments are.
+__host__ __device__ constexpr float binomf(int n, int k)
+{
+    if (k < 0 || k > n) return 0.f;
+    float r = 1.f;
+    for (int i = 1; i <= k; ++i) r = r * (float)(n - k + i) / (float)i;
+    return r;
+}
 
 __device__ __forceinline__ float factf(int n)
 {
@@ -325,7 +326,18 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
                 for (int d = 0; d <= n; ++d) P[d] = 0.f;
         }
         __syncwarp();
-        // derivatives 0..n carried from piece to piece (lane d computes coefficient d)
+        // derivatives 0..n carried from piece to piece (lane d computes coefficient d);
+        // C(k, lane) held in registers (a lane-dependent index into a constant
+        // table would serialise the warp's constant loads)
+        float cb[nc];
+#pragma unroll
+        for (int k = 0; k < nc; ++k) {
+            float c = 0.f;
+#pragma unroll
+            for (int d = 0; d <= n; ++d)
+                if (lane == d) c = binomf(k, d);
+            cb[k] = c;
+        }
         for (int pi = 1; pi < nh; ++pi) {
             if (lane <= n) {
                 const int cur = bpq[pi], prev = bpq[pi - 1];
@@ -333,7 +345,7 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
                 float sacc = 0.f;
 #pragma unroll
                 for (int k = nc - 1; k >= 0; --k)
-                    if (k >= lane) sacc = __fmaf_rn(sacc, dl, binomf(k, lane) * P[(pi - 1) * 8 + k]);
+                    if (k >= lane) sacc = __fmaf_rn(sacc, dl, cb[k] * P[(pi - 1) * 8 + k]);
                 P[pi * 8 + lane] = sacc;
             }
             __syncwarp();
@@ -358,20 +370,26 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
         __syncwarp();
         if (lane < kTabHead) tab[lane] = lane == kTabA ? a : (lane == kTabB ? b : (lane < m ? sv[lane + 1] : FLT_MAX));
         const int K = slots_of(m, a, b, two_w);
-        for (int idx = lane; idx < (m + 1) * K; idx += 32) {
-            const int sg = idx / K, i = idx - sg * K;
+        // lane = (sigma, candidate) with candidate = lane % 8, four sigmas per pass
+#pragma unroll
+        for (int pass = 0; pass < (m + 4) / 4; ++pass) {
+            const int sg = pass * 4 + (lane >> 3), i = lane & 7;
+            if (sg > m || i >= K) continue;
             const float hw = 0.5f * (((sg < m) ? sv[sg + 1] : a) - sv[sg]);
             // interval start u_lo = (i - f) a + q b; midpoint u_lo + hw
             const int pl = i - sf[sg], ql = sq[sg];
             if (sym_diff(pl - m, ql - m, a, b, hw) >= 0.f) continue;          // beyond 2w
             const bool mirror = sym_diff(2 * pl - m, 2 * ql - m, a, b, 2.f * hw) > 0.f;
+            // last piece (of the nh sorted ones) starting at or before the
+            // midpoint of the entry (mirrored into the left half if needed):
+            // binary search, the predicate being monotone in the piece index
+            const int pq = mirror ? m - pl : pl, qq = mirror ? m - ql : ql;
+            const float hs = mirror ? -hw : hw;
             int pi = 0;
-            if (!mirror) {
-                while (pi + 1 < nh && sym_diff(pl - (bpq[pi + 1] & 255), ql - (bpq[pi + 1] >> 8), a, b, hw) >= 0.f) ++pi;
-            } else {
-                while (pi + 1 < nh &&
-                       sym_diff(m - pl - (bpq[pi + 1] & 255), m - ql - (bpq[pi + 1] >> 8), a, b, -hw) >= 0.f)
-                    ++pi;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int c = pi + st;
+                if (c < nh && sym_diff(pq - (bpq[c] & 255), qq - (bpq[c] >> 8), a, b, hs) >= 0.f) pi = c;
             }
             const int bp = bpq[pi] & 255, bq = bpq[pi] >> 8;
             const float X = mirror ? sym_diff(m - pl - bp, m - ql - bq, a, b, 0.f) : sym_diff(pl - bp, ql - bq, a, b, 0.f);
