@@ -15,6 +15,11 @@ follows:
 * :func:`footprint`    phi_theta(y): Prop. 1 / eq. xsa, the convolution of the
                        two rescaled B-splines, integrated exactly piece by piece
                        with Gauss-Legendre; a Dirac replaces a zero scale.
+* :func:`box3`, :func:`footprint_box`
+                       the 3-direction box-spline of Sec. III.D from its
+                       definition (density of a sum of three uniform
+                       segments) and its exact line integral (piecewise
+                       linear along the line, trapezoid rule per piece).
 * :func:`lines_parallel`, :func:`lines_fan`, :func:`lines_points`
                        geometry -> (theta, y) with theta^perp = (sin, -cos)
                        (eq. rayparam).
@@ -52,6 +57,7 @@ _lib = None
 
 class _Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("degree", ctypes.c_int32),
+                ("basis", ctypes.c_int32),
                 ("h", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
 
 
@@ -85,6 +91,12 @@ def _load():
     lib.orc_footprint.argtypes = [ctypes.c_int, d, d, d]
     lib.orc_support_halfwidth.restype = d
     lib.orc_support_halfwidth.argtypes = [ctypes.c_int, d, d]
+    lib.orc_box3.restype = d
+    lib.orc_box3.argtypes = [d, d]
+    lib.orc_footprint_box.restype = d
+    lib.orc_footprint_box.argtypes = [d, d, d]
+    lib.orc_support_halfwidth_box.restype = d
+    lib.orc_support_halfwidth_box.argtypes = [d, d]
     lib.orc_lines_parallel.argtypes = [i32, P, i32, d, d, P, P]
     lib.orc_lines_fan.argtypes = [i32, P, d, d, i32, d, d, P, P]
     lib.orc_lines_points.argtypes = [i64, P, P, P, P]
@@ -109,22 +121,25 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _grid(nx, ny, degree, h=1.0, cx=0.0, cy=0.0) -> _Grid:
-    return _Grid(int(nx), int(ny), int(degree), float(h), float(cx), float(cy))
+def _grid(nx, ny, degree, h=1.0, cx=0.0, cy=0.0, basis=0) -> _Grid:
+    return _Grid(int(nx), int(ny), int(degree), int(basis), float(h), float(cx), float(cy))
 
 
 class Grid:
     """Coefficient grid: nx x ny nodes, spacing h, centred at (cx, cy).
 
     Node (i, j) sits at (cx + (i - (nx-1)/2) h, cy + (j - (ny-1)/2) h);
-    coefficient arrays are [ny][nx] (row j, column i fastest)."""
+    coefficient arrays are [ny][nx] (row j, column i fastest).  basis 0 is the
+    tensor-product B-spline of the given degree, basis 1 the 3-direction
+    box-spline (degree ignored)."""
 
-    def __init__(self, nx, ny, degree, h=1.0, cx=0.0, cy=0.0):
+    def __init__(self, nx, ny, degree, h=1.0, cx=0.0, cy=0.0, basis=0):
         self.nx, self.ny, self.degree = int(nx), int(ny), int(degree)
         self.h, self.cx, self.cy = float(h), float(cx), float(cy)
+        self.basis = int(basis)
 
     def _c(self) -> _Grid:
-        return _grid(self.nx, self.ny, self.degree, self.h, self.cx, self.cy)
+        return _grid(self.nx, self.ny, self.degree, self.h, self.cx, self.cy, self.basis)
 
 
 def max_threads() -> int:
@@ -142,6 +157,24 @@ def footprint(n: int, theta: float, yt: float) -> float:
 
 def footprint_cs(n: int, ct: float, st: float, yt: float) -> float:
     return float(_load().orc_footprint(int(n), float(ct), float(st), float(yt)))
+
+
+def box3(x1: float, x2: float) -> float:
+    """3-direction box-spline (directions e1, e2, e1 + e2; Sec. III.D) at (x1, x2)."""
+    return float(_load().orc_box3(float(x1), float(x2)))
+
+
+def footprint_box(theta: float, yt: float) -> float:
+    """x-ray transform of the box-spline along theta at offset yt."""
+    return float(_load().orc_footprint_box(float(np.cos(theta)), float(np.sin(theta)), float(yt)))
+
+
+def footprint_box_cs(ct: float, st: float, yt: float) -> float:
+    return float(_load().orc_footprint_box(float(ct), float(st), float(yt)))
+
+
+def support_halfwidth_box(theta: float) -> float:
+    return float(_load().orc_support_halfwidth_box(float(np.cos(theta)), float(np.sin(theta))))
 
 
 def support_halfwidth(n: int, theta: float) -> float:

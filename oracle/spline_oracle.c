@@ -46,7 +46,8 @@
 
 typedef struct {
     int32_t nx, ny;   /* coefficients per row (x1 direction), rows (x2) */
-    int32_t degree;   /* spline degree n */
+    int32_t degree;   /* spline degree n (tensor-product B-splines) */
+    int32_t basis;    /* 0: tensor-product B-spline, 1: 3-direction box-spline */
     double h;         /* grid spacing */
     double cx, cy;    /* grid centre */
 } orc_grid;
@@ -91,6 +92,7 @@ static int cmp_double(const void *a, const void *b)
     double x = *(const double *)a, y = *(const double *)b;
     return (x > y) - (x < y);
 }
+static int cmp_double_fwd(const void *a, const void *b) { return cmp_double(a, b); }
 
 /* ------------------------------------------------------------------ */
 /* B-spline and footprint                                              */
@@ -159,6 +161,60 @@ double orc_footprint(int n, double ct, double st, double yt)
         acc += hw * s;
     }
     return acc;
+}
+
+/* ------------------------------------------------------------------ */
+/* 3-direction box-spline (Sec. III.D)                                 */
+/* ------------------------------------------------------------------ */
+
+/* The box-spline with directions u1 = e1, u2 = e2, u3 = e1 + e2 and
+ * centred unit rectangles as factors (Sec. III.D): the density of
+ * x = t1 u1 + t2 u2 + t3 u3 with t1, t2, t3 independent and uniform on
+ * [-1/2, 1/2].  Given x and t3, (t1, t2) = (x1 - t3, x2 - t3) is fixed (unit
+ * Jacobian), so M(x) is the length of the set of t3 in [-1/2, 1/2] with
+ * x1 - t3 and x2 - t3 both in [-1/2, 1/2]. */
+double orc_box3(double x1, double x2)
+{
+    double lo = fmax(-0.5, fmax(x1 - 0.5, x2 - 0.5));
+    double hi = fmin(0.5, fmin(x1 + 0.5, x2 + 0.5));
+    return hi > lo ? hi - lo : 0.0;
+}
+
+static int cmp_double_fwd(const void *a, const void *b);
+
+/* phi_theta(yt) for the box-spline: its line integral along direction
+ * (ct, st) at offset yt, int M(yt theta^perp + t theta) dt with
+ * theta^perp = (st, -ct) (eq. rayparam, eq. eqproj).  M is linear on the
+ * triangles cut by the lines x1, x2, x1 - x2 in {-1, 0, 1}, so along the line
+ * it is piecewise linear between the crossings of those lines; the
+ * trapezoid rule between consecutive crossings is exact. */
+double orc_footprint_box(double ct, double st, double yt)
+{
+    double px = yt * st, py = -yt * ct;     /* a point of the line */
+    double tb[16];
+    int nt = 0;
+    for (int k = -1; k <= 1; ++k) {
+        if (ct != 0.0) tb[nt++] = (k - px) / ct;                    /* x1 = k */
+        if (st != 0.0) tb[nt++] = (k - py) / st;                    /* x2 = k */
+        if (ct != st) tb[nt++] = (k - (px - py)) / (ct - st);       /* x1 - x2 = k */
+    }
+    qsort(tb, (size_t)nt, sizeof(double), cmp_double_fwd);
+    double acc = 0.0;
+    for (int i = 0; i + 1 < nt; ++i) {
+        double t0 = tb[i], t1 = tb[i + 1];
+        if (!(t1 > t0)) continue;
+        double m0 = orc_box3(px + t0 * ct, py + t0 * st);
+        double m1 = orc_box3(px + t1 * ct, py + t1 * st);
+        acc += 0.5 * (t1 - t0) * (m0 + m1);
+    }
+    return acc;
+}
+
+/* Half-width of the support of the box-spline's phi_theta: half the sum of
+ * |<theta^perp, u_d>| over the three directions. */
+double orc_support_halfwidth_box(double ct, double st)
+{
+    return 0.5 * (fabs(st) + fabs(ct) + fabs(st - ct));
 }
 
 /* Half-width of the support of phi_theta: (n+1)(|cos|+|sin|)/2. */
@@ -235,6 +291,16 @@ static double offset_yt(const orc_grid *g, double ct, double st, double y, int32
     return (y - (node_x1(g, i) * st - node_x2(g, j) * ct)) / g->h;
 }
 
+/* Footprint and support half-width of the grid's basis. */
+static double footprint_g(const orc_grid *g, double ct, double st, double yt)
+{
+    return g->basis == 1 ? orc_footprint_box(ct, st, yt) : orc_footprint(g->degree, ct, st, yt);
+}
+static double halfwidth_g(const orc_grid *g, double ct, double st)
+{
+    return g->basis == 1 ? orc_support_halfwidth_box(ct, st) : orc_support_halfwidth(g->degree, ct, st);
+}
+
 /* Is (i, j) in the support of the ray?  Open support |yt| < w, except
  * for degree 0 along an axis where the footprint is a rectangle with the
  * midpoint value at its edges, so |yt| <= w. */
@@ -267,10 +333,10 @@ static void row_range(const orc_grid *g, double ct, double st, double y, double 
 
 static double forward_one(const orc_grid *g, const double *coef, double th, double y, int brute)
 {
-    int n = g->degree;
+    int n = g->basis == 1 ? 1 : g->degree;
     double ct = cos(th), st = sin(th);
     double b = fmin(fabs(ct), fabs(st));
-    double w = orc_support_halfwidth(n, ct, st);
+    double w = halfwidth_g(g, ct, st);
     double acc = 0.0;
     for (int32_t j = 0; j < g->ny; ++j) {
         int32_t i0, i1;
@@ -278,7 +344,7 @@ static double forward_one(const orc_grid *g, const double *coef, double th, doub
         for (int32_t i = i0; i <= i1; ++i) {
             double yt = offset_yt(g, ct, st, y, i, j);
             if (!in_support(n, b, yt, w)) continue;
-            acc += coef[(int64_t)j * g->nx + i] * orc_footprint(n, ct, st, yt);
+            acc += coef[(int64_t)j * g->nx + i] * footprint_g(g, ct, st, yt);
         }
     }
     return g->h * acc;
@@ -304,7 +370,7 @@ void orc_adjoint_pixels(const orc_grid *g, const double *sino, int64_t n_lines,
                         const double *theta, const double *y,
                         int64_t n_pix, const int64_t *pix, double *out, int32_t n_threads)
 {
-    int n = g->degree;
+    int n = g->basis == 1 ? 1 : g->degree;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 4)
@@ -315,10 +381,10 @@ void orc_adjoint_pixels(const orc_grid *g, const double *sino, int64_t n_lines,
         for (int64_t r = 0; r < n_lines; ++r) {
             double ct = cos(theta[r]), st = sin(theta[r]);
             double b = fmin(fabs(ct), fabs(st));
-            double w = orc_support_halfwidth(n, ct, st);
+            double w = halfwidth_g(g, ct, st);
             double yt = offset_yt(g, ct, st, y[r], i, j);
             if (!in_support(n, b, yt, w)) continue;
-            acc += sino[r] * orc_footprint(n, ct, st, yt);
+            acc += sino[r] * footprint_g(g, ct, st, yt);
         }
         out[q] = g->h * acc;
     }
@@ -342,12 +408,12 @@ void orc_visited(const orc_grid *g, int64_t n_lines, const double *theta, const 
                  int32_t brute, int64_t *counts, const int64_t *offs, int64_t *idx,
                  double *min_gap)
 {
-    int n = g->degree;
+    int n = g->basis == 1 ? 1 : g->degree;
     double gap = INFINITY;
     for (int64_t r = 0; r < n_lines; ++r) {
         double ct = cos(theta[r]), st = sin(theta[r]);
         double b = fmin(fabs(ct), fabs(st));
-        double w = orc_support_halfwidth(n, ct, st);
+        double w = halfwidth_g(g, ct, st);
         int64_t c = 0;
         for (int32_t j = 0; j < g->ny; ++j) {
             int32_t i0, i1;
