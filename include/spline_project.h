@@ -9,7 +9,8 @@
  * Image model (eq. def_f, eq. xrtbasis, Sec. III.C):
  *   f(x) = sum_k c_k phi((x - x_k)/h),  phi(x1, x2) = beta^n(x1) beta^n(x2),
  *   node k = (i, j) at x_k = (cx + (i - (nx-1)/2) h, cy + (j - (ny-1)/2) h),
- *   beta^n the centred B-spline of degree n = 0..3.
+ *   beta^n the centred B-spline of degree n = 0..3 (or the 3-direction
+ *   box-spline of Sec. III.D, see sp_basis).
  * Lines (eq. rayparam): {t theta + y theta^perp}, theta = (cos, sin),
  *   theta^perp = (sin, -cos).
  * Forward (eq. xray with eq. xrtbasis, discretised operator of Sec. IV.A):
@@ -53,11 +54,25 @@ typedef enum sp_status {
     SP_EUNSUPPORTED = -5   /* valid request that this build does not support */
 } sp_status;
 
-/* Coefficient grid: nx x ny nodes, spacing h > 0, centre (cx, cy), degree n. */
+/* Basis functions (Sec. III.D).
+ *   SP_BASIS_BSPLINE: phi(x1, x2) = beta^n(x1) beta^n(x2), the tensor-product
+ *     B-spline of degree n = grid.degree (0..3).
+ *   SP_BASIS_BOX3: the 3-direction box-spline with directions e1, e2,
+ *     e1 + e2 and centred unit rectangles as factors: the piecewise-linear
+ *     hat M(x) = max(0, 1 + min(x1, x2, 0) - max(x1, x2, 0)) on the
+ *     triangulation by x1, x2, x1 - x2 in Z (grid.degree must be 1).  Its
+ *     x-ray transform is the convolution of three boxes of widths |sin|,
+ *     |cos| and |sin - cos| (|<theta^perp, u_d>|, Prop. 1 with D = 3). */
+typedef enum sp_basis {
+    SP_BASIS_BSPLINE = 0,
+    SP_BASIS_BOX3 = 1
+} sp_basis;
+
+/* Coefficient grid: nx x ny nodes, spacing h > 0, centre (cx, cy), basis. */
 typedef struct sp_grid {
     int32_t nx, ny;        /* 1 <= nx, ny <= 16384 */
-    int32_t degree;        /* spline degree n, 0..3 */
-    int32_t reserved;      /* must be 0 */
+    int32_t degree;        /* B-spline degree n, 0..3 (1 for SP_BASIS_BOX3) */
+    int32_t basis;         /* sp_basis */
     float h;               /* grid spacing */
     float cx, cy;          /* grid centre */
 } sp_grid;
@@ -127,10 +142,11 @@ sp_status spline_lines_expand(const sp_lines *lines, float *theta_out, float *y_
 
 /*
  * The footprint phi_theta(yt) on the unit grid (Prop. 1, eq. xsa) as the
- * projector evaluates it: out[r] = phi_{theta[r]}(yt[r]) for r < count.
+ * projector evaluates it: out[r] = phi_{theta[r]}(yt[r]) for r < count, for
+ * the basis and degree of *grid (its other fields are not used).
  * theta, yt, out: device float [count].  For testing and inspection.
  */
-sp_status spline_footprint_eval(int32_t degree, int64_t count, const float *theta,
+sp_status spline_footprint_eval(const sp_grid *grid, int64_t count, const float *theta,
                                 const float *yt, float *out, void *stream);
 
 /*

@@ -14,6 +14,7 @@ import torch
 from . import build as _build
 
 SP_OK, SP_EINVAL, SP_ENOMEM, SP_ECUDA, SP_EUNSUPPORTED = 0, -1, -2, -3, -5
+BASIS_BSPLINE, BASIS_BOX3 = 0, 1
 KIND_THETA_Y, KIND_POINTS, KIND_PARALLEL, KIND_FAN = 0, 1, 2, 3
 
 _lib = None
@@ -21,7 +22,7 @@ _lib = None
 
 class SpGrid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("degree", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("h", ctypes.c_float), ("cx", ctypes.c_float),
+                ("basis", ctypes.c_int32), ("h", ctypes.c_float), ("cx", ctypes.c_float),
                 ("cy", ctypes.c_float)]
 
 
@@ -63,7 +64,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
     for name, args in (("spline_project_fwd", [G, P, L, P, P]),
                        ("spline_project_adj", [G, P, L, P, P]),
                        ("spline_lines_expand", [L, P, P, P]),
-                       ("spline_footprint_eval", [ctypes.c_int32, ctypes.c_int64, P, P, P, P]),
+                       ("spline_footprint_eval", [G, ctypes.c_int64, P, P, P, P]),
                        ("spline_visited", [G, L, P, P, P, P])):
         f = getattr(lib, name)
         f.restype = st
@@ -115,16 +116,19 @@ def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
 
 @dataclass
 class Grid:
-    """nx x ny nodes with spacing h centred at (cx, cy); spline degree 0..3."""
+    """nx x ny nodes with spacing h centred at (cx, cy).  basis BASIS_BSPLINE:
+    tensor-product B-splines of degree 0..3; BASIS_BOX3: the 3-direction
+    box-spline (degree 1)."""
     nx: int
     ny: int
     degree: int
     h: float = 1.0
     cx: float = 0.0
     cy: float = 0.0
+    basis: int = BASIS_BSPLINE
 
     def c(self) -> SpGrid:
-        return SpGrid(int(self.nx), int(self.ny), int(self.degree), 0, float(self.h),
+        return SpGrid(int(self.nx), int(self.ny), int(self.degree), int(self.basis), float(self.h),
                       float(self.cx), float(self.cy))
 
 
@@ -210,10 +214,12 @@ def spline_lines_expand(lines: Lines, device=None, stream=None):
     return th, yy
 
 
-def spline_footprint_eval(degree: int, theta: torch.Tensor, yt: torch.Tensor, stream=None) -> torch.Tensor:
+def spline_footprint_eval(degree: int, theta: torch.Tensor, yt: torch.Tensor, stream=None,
+                          basis: int = BASIS_BSPLINE) -> torch.Tensor:
     th, y = _dev_f32(theta, "theta"), _dev_f32(yt, "yt")
     out = torch.empty_like(th)
-    _check(load().spline_footprint_eval(int(degree), th.numel(), th.data_ptr(), y.data_ptr(),
+    g = SpGrid(1, 1, int(degree), int(basis), 1.0, 0.0, 0.0)
+    _check(load().spline_footprint_eval(ctypes.byref(g), th.numel(), th.data_ptr(), y.data_ptr(),
                                         out.data_ptr(), _stream(stream)))
     return out
 

@@ -72,10 +72,13 @@ sp_status check_grid(const sp_grid *g, spx::GridDev *out)
     if (g->nx < 1 || g->ny < 1 || g->nx > 16384 || g->ny > 16384)
         return fail(SP_EINVAL, "grid size must be in [1, 16384]");
     if (g->degree < 0 || g->degree > 3) return fail(SP_EINVAL, "degree must be 0..3");
-    if (g->reserved != 0) return fail(SP_EINVAL, "grid.reserved must be 0");
+    if (g->basis != SP_BASIS_BSPLINE && g->basis != SP_BASIS_BOX3) return fail(SP_EINVAL, "unknown grid.basis");
+    if (g->basis == SP_BASIS_BOX3 && g->degree != 1)
+        return fail(SP_EINVAL, "the 3-direction box-spline needs grid.degree = 1");
     if (!finite(g->h) || !(g->h > 0.f)) return fail(SP_EINVAL, "grid spacing h must be finite and > 0");
     if (!finite(g->cx) || !finite(g->cy)) return fail(SP_EINVAL, "grid centre must be finite");
-    *out = spx::GridDev{g->nx, g->ny, g->degree, g->h, g->cx, g->cy};
+    *out = spx::GridDev{g->nx, g->ny, g->degree, g->basis, g->basis == SP_BASIS_BOX3 ? 2 : g->degree,
+                        g->h, g->cx, g->cy};
     return SP_OK;
 }
 
@@ -256,18 +259,25 @@ sp_status spline_lines_expand(const sp_lines *lines, float *theta_out, float *y_
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "line expansion");
 }
 
-sp_status spline_footprint_eval(int32_t degree, int64_t count, const float *theta, const float *yt,
+sp_status spline_footprint_eval(const sp_grid *grid, int64_t count, const float *theta, const float *yt,
                                 float *out, void *stream)
 {
     g_err.clear();
-    if (degree < 0 || degree > 3) return fail(SP_EINVAL, "degree must be 0..3");
+    if (!grid) return fail(SP_EINVAL, "grid is NULL");
+    sp_grid gg = *grid;
+    gg.nx = gg.ny = 1;
+    gg.h = 1.f;
+    gg.cx = gg.cy = 0.f;
+    spx::GridDev g;
+    sp_status st0 = check_grid(&gg, &g);
+    if (st0 != SP_OK) return st0;
     if (count < 0) return fail(SP_EINVAL, "count must be >= 0");
     if (count == 0) return SP_OK;
     if (!theta || !yt || !out) return fail(SP_EINVAL, "NULL pointer");
     void *ws = nullptr;
     sp_status st = workspace(sizeof(float) * (size_t)spx::kTabFloats * (size_t)count, &ws);
     if (st != SP_OK) return st;
-    cudaError_t e = spx::launch_footprint_eval(degree, count, theta, yt, out, static_cast<float *>(ws),
+    cudaError_t e = spx::launch_footprint_eval(g, count, theta, yt, out, static_cast<float *>(ws),
                                                static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "footprint evaluation");
 }

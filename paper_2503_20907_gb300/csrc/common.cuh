@@ -45,6 +45,7 @@ constexpr int kMaxK = 2 * kMaxM;              // candidate slots per row
 constexpr int kNC = 2 * kMaxDeg + 2;          // coefficients of one polynomial
 constexpr int kSigStride = kMaxK * kNC;       // 64 floats
 constexpr int kTabHead = 8;                   // s_1..s_m (padded with FLT_MAX), a, b
+constexpr int kTabMode = 5;                   // head slot of the footprint kind (TabMode)
 constexpr int kTabA = 6;                      // head slot of the a the table was built with
 constexpr int kTabB = 7;                      // head slot of its b
 constexpr int kTabFloats = kTabHead + kMaxSig * kSigStride;   // 328 floats
@@ -56,6 +57,13 @@ __host__ __device__ constexpr int tab_poly(int sg, int i)
 {
     return kTabHead + sg * kSigStride + i * kNC;
 }
+
+// Footprint kinds (table head slot kTabMode).
+enum TabMode : int {
+    kModeBspline = 0,   // beta^n_a * beta^n_b (Prop. 1, D = 2)
+    kModeBoxSame = 1,   // 3-direction box-spline, sin and cos of equal sign: boxes b, a, a - b
+    kModeBoxOpp = 2,    // 3-direction box-spline, opposite signs: boxes b, a, a + b
+};
 
 enum LineFlags : int {
     kVert = 1,        // rows are x2 (index j), columns x1 (index i)
@@ -85,6 +93,8 @@ static_assert(sizeof(LineHdr) == 64, "LineHdr layout");
 
 struct GridDev {
     int nx, ny, degree;
+    int basis;   // sp_basis
+    int kdeg;    // degree the kernels are instantiated for: degree, or 2 for the box-spline
     float h, cx, cy;
 };
 
@@ -247,7 +257,7 @@ cudaError_t launch_fwd_strip(const GridDev &g, const LinesDev &L, const LineHdr 
 // Adjoint with strip accumulators; coef_out is overwritten.
 cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
                              const float *sino, void *scratch, float *coef_out, int *slow_rows, cudaStream_t s);
-cudaError_t launch_footprint_eval(int degree, int64_t count, const float *theta, const float *yt,
+cudaError_t launch_footprint_eval(const GridDev &g, int64_t count, const float *theta, const float *yt,
                                   float *out, float *scratch, cudaStream_t s);
 
 

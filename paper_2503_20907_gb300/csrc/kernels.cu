@@ -105,6 +105,33 @@ __device__ __forceinline__ int slots_of(int m, float af, float bf, float two_w)
     return K < 2 * m ? K : 2 * m;
 }
 
+// Support of phi_theta in u = y~ + w: its length 2w (float, as the kernels
+// compare it), w (double), and the candidate slots K of a row.  B-splines:
+// 2w = (n+1)(a+b).  Box-spline: the three box widths b, a, a -+ b add up to
+// 2a (sin and cos of equal sign) or 2(a+b) (opposite signs).
+__device__ __forceinline__ void support_params(int kdeg, float af, float bf, int mode, float &two_w, double &w,
+                                               int &K)
+{
+    if (mode == kModeBspline) {
+        const int m = kdeg + 1;
+        two_w = two_w_of(m, af, bf);
+        w = 0.5 * m * ((double)af + (double)bf);
+        K = slots_of(m, af, bf, two_w);
+    } else {
+        const double W = (mode == kModeBoxSame) ? 2.0 * (double)af : 2.0 * ((double)af + (double)bf);
+        two_w = (float)W;
+        w = 0.5 * W;
+        const int k = (int)floorf(two_w / af) + 1;
+        K = k < 2 * (kdeg + 1) ? k : 2 * (kdeg + 1);
+    }
+}
+
+__device__ __forceinline__ int footprint_mode(int basis, double dx, double dy)
+{
+    if (basis != SP_BASIS_BOX3) return kModeBspline;
+    return (dx * dy >= 0.0) ? kModeBoxSame : kModeBoxOpp;
+}
+
 // Split x into hi + lo with hi carrying `bits` significant bits.
 __device__ void split_hi_lo(double x, int bits, float &hi, float &lo)
 {
@@ -124,20 +151,21 @@ __global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, float *tabs, i
     if (r >= M) return;
     double dx, dy, px, py;
     line_geometry(L, r, dx, dy, px, py);
-    const int m = g.degree + 1;
     LineHdr H;
     H.U0_lo = 0.f;
     H.a_corr = 0.f;
     H.tab = (L.kind == SP_LINES_PARALLEL) ? (int)(r / L.n_det) : (int)r;
     float af, bf;
-    footprint_ab(g.degree, dx, dy, af, bf);
+    footprint_ab(g.kdeg, dx, dy, af, bf);
+    const int mode = footprint_mode(g.basis, dx, dy);
     if (L.kind != SP_LINES_PARALLEL || r % L.n_det == 0) {
-        // the owner of table H.tab hands a and b to the table builder
+        // the owner of table H.tab hands a, b and the footprint kind to the table builder
         tabs[(int64_t)H.tab * kTabFloats + kTabA] = af;
         tabs[(int64_t)H.tab * kTabFloats + kTabB] = bf;
+        tabs[(int64_t)H.tab * kTabFloats + kTabMode] = (float)mode;
     }
-    H.two_w = two_w_of(m, af, bf);
-    H.K = slots_of(m, af, bf, H.two_w);
+    double w;
+    support_params(g.kdeg, af, bf, mode, H.two_w, w, H.K);
     const bool vert = fabs(dy) >= fabs(dx);
     const double A = fmax(fabs(dx), fabs(dy));
     const double B = fmin(fabs(dx), fabs(dy));
@@ -149,8 +177,7 @@ __global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, float *tabs, i
     if (vert) { kap = -dy; rho = dx; rc = jc; qc = ic; Nr = g.ny; Nq = g.nx; }
     else { kap = dx; rho = -dy; rc = ic; qc = jc; Nr = g.nx; Nq = g.ny; }
     const int sgn = kap > 0.0 ? 1 : -1;
-    // w exactly as the table sees it, m (a + b)/2 with the table's a and b
-    const double w = 0.5 * (double)m * ((double)af + (double)bf);
+    // w as the table sees it (support_params, with the table's a and b)
     int flags = (vert ? kVert : 0) | (sgn < 0 ? kKapNeg : 0);
     if (g.degree == 0 && B == 0.0) flags |= kDeg0Axis;
 
@@ -419,8 +446,149 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
     __syncwarp();
 }
 
-// One warp per table.  a and b were written into the table head by the line
-// setup (FP64 geometry stays there, once per line).
+// Table of the 3-direction box-spline (Sec. III.D), same layout as the
+// B-spline tables of kernel degree 2 (polynomials of degree <= 2 in t).
+// phi_theta is the convolution of the boxes of widths b, a and a -+ b
+// (Prop. 1 with D = 3): piecewise quadratic, C^1, with breakpoints at the
+// sums of subsets of the widths, each carrying the sign (-1)^(subset size);
+// phi'' = (sum of the signs passed) / (product of the widths).  Built
+// stably like the B-spline tables: phi and phi' are carried from piece to
+// piece with piece lengths formed from the integer coordinates (p, q) of the
+// breakpoints p a + q b, so a narrow box never divides a large sum.  A width
+// below kBMin (b near an axis, a - b near a diagonal) is a Dirac: the
+// remaining two boxes give a piecewise-linear phi.
+__device__ void build_table_box(float a, float b, int mode, float *out, float *sm, int lane)
+{
+    constexpr int K2 = 2, NSMAX = 3;          // kernel degree 2: up to 3 interval ends in the head
+    float *tab = sm;
+    float *pc = tab + kTabFloats;             // pieces: [8][3] (phi, phi', top derivative)
+    int *bp = reinterpret_cast<int *>(pc + 24);   // sorted breakpoints p | q << 8 (q biased by 4)
+    float *sv = reinterpret_cast<float *>(bp + 8);
+    int *sq = reinterpret_cast<int *>(sv + 4);
+    int *sf = sq + 4;
+    int *nbp = sf + 4;
+    for (int k = lane; k < kTabFloats; k += 32) tab[k] = 0.f;
+    __syncwarp();
+    if (lane == 0) {
+        // box widths with their coordinates: b = (0,1), a = (1,0), a -+ b = (1,-+1)
+        const int q3 = (mode == kModeBoxSame) ? -1 : 1;
+        float wv[3] = {b, a, (mode == kModeBoxSame) ? a - b : (float)((double)a + (double)b)};
+        int wp[3] = {0, 1, 1}, wq[3] = {1, 0, q3};
+        int used[3], nu = 0;
+        for (int d = 0; d < 3; ++d)
+            if (wv[d] >= kBMin) used[nu++] = d;
+        float prod = 1.f;
+        for (int u = 0; u < nu; ++u) prod *= wv[used[u]];
+        // all subset sums, sorted by value (ties by p, then q)
+        const int nb = 1 << nu;
+        int P[8], Q[8], S[8];
+        float V[8];
+        for (int e = 0; e < nb; ++e) {
+            int pp = 0, qq = 0, c = 0;
+            for (int u = 0; u < nu; ++u)
+                if ((e >> u) & 1) { pp += wp[used[u]]; qq += wq[used[u]]; ++c; }
+            int k = e;
+            const float v = __fmaf_rn((float)pp, a, (float)qq * b);
+            while (k > 0 && (V[k - 1] > v || (V[k - 1] == v && (P[k - 1] > pp || (P[k - 1] == pp && Q[k - 1] > qq))))) {
+                V[k] = V[k - 1]; P[k] = P[k - 1]; Q[k] = Q[k - 1]; S[k] = S[k - 1];
+                --k;
+            }
+            V[k] = v; P[k] = pp; Q[k] = qq; S[k] = (c & 1) ? -1 : 1;
+        }
+        // walk the pieces: phi, phi' and the top derivative (phi'' for three
+        // boxes, phi' for two) on each
+        float f0 = 0.f, f1 = 0.f;
+        int acc = 0;
+        for (int j = 0; j < nb; ++j) {
+            acc += S[j];
+            const float D = (float)acc / prod;
+            bp[j] = P[j] | ((Q[j] + 4) << 8);
+            pc[3 * j] = f0;
+            pc[3 * j + 1] = (nu == 3) ? f1 : D;
+            pc[3 * j + 2] = (nu == 3) ? 0.5f * D : 0.f;
+            if (j + 1 < nb) {
+                const float dl = sym_diff(P[j + 1] - P[j], Q[j + 1] - Q[j], a, b, 0.f);
+                if (nu == 3) {
+                    f0 = __fmaf_rn(__fmaf_rn(0.5f * D, dl, f1), dl, f0);
+                    f1 = __fmaf_rn(D, dl, f1);
+                } else {
+                    f0 = __fmaf_rn(D, dl, f0);
+                }
+            }
+        }
+        *nbp = nb;
+        // interval ends s = (q b) mod a in (0, a] for the q of the widths used
+        int qs[2], nq = 0;
+        for (int u = 0; u < nu; ++u) {
+            const int qq = wq[used[u]];
+            if (qq != 0 && (nq == 0 || qs[0] != qq)) qs[nq++] = qq;
+        }
+        if (mode == kModeBoxOpp && nu == 3) qs[nq++] = 2;   // b + (a + b) = a + 2b
+        const float ainv = 1.0f / a;
+        float rs[3];
+        int fs[3], qv[3];
+        for (int t = 0; t < nq; ++t) {
+            const int qq = qs[t];
+            int fq = (int)floorf((float)qq * b * ainv);
+            float rq = __fmaf_rn((float)(-fq), a, (float)qq * b);
+            if (rq <= 0.f) { fq -= 1; rq = __fmaf_rn((float)(-fq), a, (float)qq * b); }
+            else if (rq > a) { fq += 1; rq = __fmaf_rn((float)(-fq), a, (float)qq * b); }
+            int k = t;
+            while (k > 0 && rs[k - 1] > rq) { rs[k] = rs[k - 1]; fs[k] = fs[k - 1]; qv[k] = qv[k - 1]; --k; }
+            rs[k] = rq; fs[k] = fq; qv[k] = qq;
+        }
+        sv[0] = 0.f; sq[0] = 0; sf[0] = 0;
+        for (int t = 0; t < nq; ++t) { sv[t + 1] = rs[t]; sq[t + 1] = qv[t]; sf[t + 1] = fs[t]; }
+        for (int t = nq + 1; t <= NSMAX; ++t) { sv[t] = a; sq[t] = 0; sf[t] = -1; }
+        for (int t = 0; t < kTabHead; ++t) tab[t] = FLT_MAX;
+        for (int t = 0; t < nq; ++t) tab[t] = rs[t];
+        tab[kTabMode] = (float)mode;
+        tab[kTabA] = a;
+        tab[kTabB] = b;
+    }
+    __syncwarp();
+    // entries: lane = (interval sg, candidate i)
+    const int nb = *nbp;
+    const int sg = lane >> 3, i = lane & 7;
+    const int nsg = NSMAX;   // intervals (s_sg, s_sg+1], sg = 0..2
+    if (sg < nsg && i < 2 * (K2 + 1)) {
+        const float hw = 0.5f * (sv[sg + 1] - sv[sg]);
+        const int pl = i - sf[sg], ql = sq[sg];
+        const int top = bp[nb - 1];
+        const int ptop = top & 255, qtop = (top >> 8) - 4;
+        // entry inside the support: its midpoint below the last breakpoint.
+        // Empty intervals (hw = 0) are filled too, with the expansion just
+        // right of their start: rows step by the exact |kappa|, which can
+        // exceed the table's float a by an ulp, and a u_0 in that gap lands
+        // in an empty last interval.
+        if (sym_diff(pl - ptop, ql - qtop, a, b, hw) < 0.f) {
+            int pi = 0;
+#pragma unroll
+            for (int st = 4; st > 0; st >>= 1) {
+                const int c = pi + st;
+                if (c < nb - 1) {
+                    const int bc = bp[c];
+                    if (sym_diff(pl - (bc & 255), ql - ((bc >> 8) - 4), a, b, hw) >= 0.f) pi = c;
+                }
+            }
+            const int bc = bp[pi];
+            const float X = sym_diff(pl - (bc & 255), ql - ((bc >> 8) - 4), a, b, 0.f);
+            const float c0 = pc[3 * pi], c1 = pc[3 * pi + 1], c2 = pc[3 * pi + 2];
+            float *T = tab + tab_poly(sg, i);
+            T[0] = __fmaf_rn(__fmaf_rn(c2, X, c1), X, c0);
+            T[1] = __fmaf_rn(2.f * c2, X, c1);
+            T[2] = c2;
+        }
+    }
+    __syncwarp();
+    if (out)
+        for (int k = lane; k < kTabFloats / 4; k += 32)
+            reinterpret_cast<float4 *>(out)[k] = reinterpret_cast<const float4 *>(tab)[k];
+    __syncwarp();
+}
+
+// One warp per table.  a, b and the footprint kind were written into the
+// table head by the line setup (FP64 geometry stays there, once per line).
 template <int DEG>
 __global__ void __launch_bounds__(kTabWarps * 32) tables_kernel(float *tabs, int64_t n_tab)
 {
@@ -430,8 +598,10 @@ __global__ void __launch_bounds__(kTabWarps * 32) tables_kernel(float *tabs, int
     if (t >= n_tab) return;
     float *out = tabs + t * (int64_t)kTabFloats;
     const float af = out[kTabA], bf = out[kTabB];
+    const int mode = (int)out[kTabMode];
     __syncwarp();
-    build_table_warp<DEG>(af, bf, out, scratch[warp], lane);
+    if (DEG == 2 && mode != kModeBspline) build_table_box(af, bf, mode, out, scratch[warp], lane);
+    else build_table_warp<DEG>(af, bf, out, scratch[warp], lane);
 }
 
 // ------------------------------------------------------------------ evaluation
@@ -611,14 +781,16 @@ __global__ void expand_kernel(LinesDev L, int64_t M, float *theta_out, float *y_
 }
 
 template <int DEG>
-__device__ float footprint_from_table(const float *tab, float a, float b, float yt)
+__device__ float footprint_from_table(const float *tab, float a, float b, int mode, float yt)
 {
     // The offset is split in double so that the probe measures the table only.
-    const int m = DEG + 1;
-    const float two_w = two_w_of(m, a, b);
-    const double u = (double)yt + 0.5 * (double)m * ((double)a + (double)b);
+    float two_w;
+    double w;
+    int K;
+    support_params(DEG, a, b, mode, two_w, w, K);
+    const double u = (double)yt + w;
     const bool ties = (DEG == 0) && (b == 0.f);
-    const double tw = (double)m * ((double)a + (double)b);
+    const double tw = 2.0 * w;
     if (ties) {
         if (u < 0.0 || u > tw) return 0.f;
         if (u == 0.0 || u == tw) return 0.5f / a;
@@ -629,7 +801,6 @@ __device__ float footprint_from_table(const float *tab, float a, float b, float 
     double u0d = u - (double)i * (double)a;
     if (u0d <= 0.0) { i -= 1; u0d += (double)a; }
     else if (u0d > (double)a) { i += 1; u0d -= (double)a; }
-    const int K = slots_of(m, a, b, two_w);
     if (i < 0 || i >= K) return 0.f;
     float s_lo;
     const float u0 = (float)u0d;
@@ -638,7 +809,7 @@ __device__ float footprint_from_table(const float *tab, float a, float b, float 
 }
 
 template <int DEG>
-__global__ void footprint_eval_kernel(int64_t count, const float *theta, const float *yt, float *out)
+__global__ void footprint_eval_kernel(int64_t count, const float *theta, const float *yt, float *out, int basis)
 {
     __shared__ __align__(16) float scratch[kTabWarps][kBuildScratch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -648,8 +819,10 @@ __global__ void footprint_eval_kernel(int64_t count, const float *theta, const f
     sincos((double)theta[r], &s, &c);
     float af, bf;
     footprint_ab(DEG, c, s, af, bf);
-    build_table_warp<DEG>(af, bf, nullptr, scratch[warp], lane);
-    if (lane == 0) out[r] = footprint_from_table<DEG>(scratch[warp], af, bf, yt[r]);
+    const int mode = footprint_mode(basis, c, s);
+    if (DEG == 2 && mode != kModeBspline) build_table_box(af, bf, mode, nullptr, scratch[warp], lane);
+    else build_table_warp<DEG>(af, bf, nullptr, scratch[warp], lane);
+    if (lane == 0) out[r] = footprint_from_table<DEG>(scratch[warp], af, bf, mode, yt[r]);
 }
 
 inline unsigned blocks_for(int64_t n, int per)
@@ -688,7 +861,7 @@ cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int6
 {
     (void)L;
     if (n_tab <= 0) return cudaSuccess;
-    SPX_DISPATCH(g.degree, tables_kernel, blocks_for(n_tab, kTabWarps), kTabWarps * 32, s, tabs, n_tab);
+    SPX_DISPATCH(g.kdeg, tables_kernel, blocks_for(n_tab, kTabWarps), kTabWarps * 32, s, tabs, n_tab);
     return cudaGetLastError();
 }
 
@@ -696,7 +869,7 @@ cudaError_t launch_fwd(const GridDev &g, const LineHdr *hdr, const float *tabs, 
                        const float *coef, float *sino, cudaStream_t s)
 {
     if (m <= 0) return cudaSuccess;
-    SPX_DISPATCH(g.degree, fwd_kernel, warp_blocks(m), 256, s, g, hdr, tabs, m, coef, sino);
+    SPX_DISPATCH(g.kdeg, fwd_kernel, warp_blocks(m), 256, s, g, hdr, tabs, m, coef, sino);
     return cudaGetLastError();
 }
 
@@ -705,7 +878,7 @@ cudaError_t launch_adj(const GridDev &g, const LineHdr *hdr, const float *tabs, 
 {
     cudaError_t e = cudaMemsetAsync(coef_out, 0, sizeof(float) * (size_t)g.nx * (size_t)g.ny, s);
     if (e != cudaSuccess || m <= 0) return e;
-    SPX_DISPATCH(g.degree, adj_kernel, warp_blocks(m), 256, s, g, hdr, tabs, m, sino, coef_out);
+    SPX_DISPATCH(g.kdeg, adj_kernel, warp_blocks(m), 256, s, g, hdr, tabs, m, sino, coef_out);
     return cudaGetLastError();
 }
 
@@ -714,7 +887,7 @@ cudaError_t launch_visited(const GridDev &g, const LineHdr *hdr, const float *ta
                            cudaStream_t s)
 {
     if (m <= 0) return cudaSuccess;
-    SPX_DISPATCH(g.degree, visited_kernel, warp_blocks(m), 256, s, g, hdr, tabs, m, counts,
+    SPX_DISPATCH(g.kdeg, visited_kernel, warp_blocks(m), 256, s, g, hdr, tabs, m, counts,
                  offsets, nodes);
     return cudaGetLastError();
 }
@@ -726,13 +899,13 @@ cudaError_t launch_expand(const LinesDev &L, float *theta_out, float *y_out, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_footprint_eval(int degree, int64_t count, const float *theta, const float *yt,
+cudaError_t launch_footprint_eval(const GridDev &g, int64_t count, const float *theta, const float *yt,
                                   float *out, float *scratch, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
     (void)scratch;
-    SPX_DISPATCH(degree, footprint_eval_kernel, blocks_for(count, kTabWarps), kTabWarps * 32, s, count, theta, yt,
-                 out);
+    SPX_DISPATCH(g.kdeg, footprint_eval_kernel, blocks_for(count, kTabWarps), kTabWarps * 32, s, count, theta, yt,
+                 out, g.basis);
     return cudaGetLastError();
 }
 

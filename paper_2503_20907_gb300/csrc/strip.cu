@@ -554,7 +554,7 @@ cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *h
 
 bool strip_supported(const GridDev &g, const LinesDev &L)
 {
-    return (L.kind == SP_LINES_PARALLEL || L.kind == SP_LINES_FAN) && g.degree >= 1;
+    return (L.kind == SP_LINES_PARALLEL || L.kind == SP_LINES_FAN) && g.kdeg >= 1;
 }
 
 size_t strip_scratch_bytes(const GridDev &g) { return sizeof(float) * (size_t)g.nx * g.ny + 256; }
@@ -563,7 +563,7 @@ cudaError_t launch_fwd_strip(const GridDev &g, const LinesDev &L, const LineHdr 
                              const float *coef, void *scratch, float *sino, int *err, cudaStream_t s)
 {
     float *coefT = static_cast<float *>(scratch);
-    switch (g.degree) {
+    switch (g.kdeg) {
     case 1: return launch_strip_t<1, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
     case 2: return launch_strip_t<2, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
     default: return launch_strip_t<3, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
@@ -575,7 +575,7 @@ cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr 
 {
     float *outT = static_cast<float *>(scratch);
     float *p = const_cast<float *>(sino);
-    switch (g.degree) {
+    switch (g.kdeg) {
     case 1: return launch_strip_t<1, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);
     case 2: return launch_strip_t<2, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);
     default: return launch_strip_t<3, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);

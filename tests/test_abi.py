@@ -65,5 +65,11 @@ def test_host_side_argument_checks(lib):
     assert lib.sp_lines_count(ctypes.byref(fan)) == 15
     fan.m = 14                                         # inconsistent count
     assert lib.sp_lines_count(ctypes.byref(fan)) == -1
-    assert lib.spline_footprint_eval(9, 3, 1, 1, 1, None) == L.SP_EINVAL
+    g9 = L.SpGrid(1, 1, 9, 0, 1.0, 0.0, 0.0)          # degree out of range
+    assert lib.spline_footprint_eval(ctypes.byref(g9), 3, 1, 1, 1, None) == L.SP_EINVAL
+    gb = L.SpGrid(8, 8, 3, L.BASIS_BOX3, 1.0, 0.0, 0.0)   # the box-spline needs degree 1
+    assert lib.spline_project_fwd(ctypes.byref(gb), 1, ctypes.byref(fan), 1, None) == L.SP_EINVAL
+    assert b"box" in lib.sp_last_error()
+    gu = L.SpGrid(8, 8, 1, 5, 1.0, 0.0, 0.0)          # unknown basis
+    assert lib.spline_project_fwd(ctypes.byref(gu), 1, ctypes.byref(fan), 1, None) == L.SP_EINVAL
     assert lib.sp_version() >= 100
