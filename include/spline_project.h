@@ -206,6 +206,57 @@ sp_status spline_plan_adj(const sp_plan *plan, const float *sino, float *coef_ou
  */
 sp_status spline_plan_cgls(sp_plan *plan, const float *b, float *x, int32_t iters,
                            double *gamma_hist, void *stream);
+/*
+ * Kernel choice of a plan, per direction: 0 = automatic (the strip kernels
+ * for PARALLEL and FAN lines of kernel degree >= 1, else the general
+ * kernels), 1 = strip kernels where they apply, 2 = general kernels
+ * (warp per line).  Both give the same results within rounding (no paper
+ * counterpart: this is an implementation choice).
+ */
+sp_status spline_plan_set_paths(sp_plan *plan, int32_t fwd_path, int32_t adj_path);
+/*
+ * Autotuner: times the forward and the adjoint with both kernel families on
+ * the caller's data (coef: device [ny][nx], sino: device [m]; neither is
+ * modified; outputs go to temporary buffers) and keeps the faster per
+ * direction (spline_plan_set_paths).  Writes the choices to *fwd_path and
+ * *adj_path and, if ms != NULL, the mean times ms[0..3] = forward strip,
+ * forward general, adjoint strip, adjoint general (0 when not measured).
+ * Synchronises the stream; allocates and frees m + ny*nx floats.
+ */
+sp_status spline_plan_autotune(sp_plan *plan, const float *coef, const float *sino, void *stream,
+                               int32_t *fwd_path, int32_t *adj_path, float *ms);
+
+/*
+ * Batches: several independent instances (each its own grid, basis, degree
+ * and line list, sizes free) projected together.  A call forks the
+ * instances over 8 internal streams and joins them on the caller's stream;
+ * the first call for a given set of data pointers records that as a CUDA
+ * graph, later calls with the same pointers replay it (one launch).
+ *   spline_batch_create   count >= 1 instances from grids[count], lines[count]
+ *                         (each as spline_plan_create; all pointers of
+ *                         lines must stay valid while the batch is prepared)
+ *   spline_batch_prepare  line setup and tables of every instance
+ *   spline_batch_fwd      sino[i] = A_i coef[i] for every i; coef and sino
+ *                         are HOST arrays of count DEVICE pointers
+ *   spline_batch_adj      coef_out[i] = A_i^T sino[i]
+ *   spline_batch_autotune spline_plan_autotune on each instance; paths
+ *                         (NULL or host int32 [2 count]) receives the forward
+ *                         and adjoint choice of each; drops recorded graphs
+ *   spline_batch_destroy  frees everything (synchronises the device)
+ * Calls on one batch must be ordered; capture of the graph needs the
+ * device not to be capturing on the calling thread already.
+ */
+typedef struct sp_batch sp_batch;
+sp_status spline_batch_create(int32_t count, const sp_grid *grids, const sp_lines *lines, sp_batch **batch);
+sp_status spline_batch_prepare(sp_batch *batch, void *stream);
+sp_status spline_batch_fwd(sp_batch *batch, const float *const *coef, float *const *sino, void *stream);
+sp_status spline_batch_adj(sp_batch *batch, const float *const *sino, float *const *coef_out, void *stream);
+sp_status spline_batch_autotune(sp_batch *batch, const float *const *coef, const float *const *sino,
+                                void *stream, int32_t *paths);
+/* Number of instances (-1 if batch is NULL). */
+int32_t spline_batch_count(const sp_batch *batch);
+sp_status spline_batch_destroy(sp_batch *batch);
+
 /* Number of lines of the plan (-1 if plan is NULL). */
 int64_t spline_plan_lines(const sp_plan *plan);
 /*

@@ -45,7 +45,9 @@ EXPORTED = ("sp_lines_count", "spline_project_fwd", "spline_project_adj", "splin
             "spline_footprint_eval", "spline_visited", "sp_release_workspace", "sp_last_error",
             "sp_version", "spline_plan_create", "spline_plan_prepare", "spline_plan_fwd",
             "spline_plan_adj", "spline_plan_lines", "spline_plan_destroy", "spline_plan_stats",
-            "spline_project_fwd_noalloc", "spline_plan_cgls")
+            "spline_project_fwd_noalloc", "spline_plan_cgls", "spline_plan_set_paths",
+            "spline_plan_autotune", "spline_batch_create", "spline_batch_prepare", "spline_batch_fwd",
+            "spline_batch_adj", "spline_batch_autotune", "spline_batch_count", "spline_batch_destroy")
 
 
 def load(build_if_stale: bool = True) -> ctypes.CDLL:
@@ -85,6 +87,24 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
     lib.spline_project_fwd_noalloc.argtypes = [G, P, L, P, P]
     lib.spline_plan_cgls.restype = st
     lib.spline_plan_cgls.argtypes = [P, P, P, ctypes.c_int32, P, P]
+    lib.spline_plan_set_paths.restype = st
+    lib.spline_plan_set_paths.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+    lib.spline_plan_autotune.restype = st
+    lib.spline_plan_autotune.argtypes = [P, P, P, P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_float)]
+    lib.spline_batch_create.restype = st
+    lib.spline_batch_create.argtypes = [ctypes.c_int32, G, L, ctypes.POINTER(ctypes.c_void_p)]
+    for name in ("spline_batch_fwd", "spline_batch_adj"):
+        getattr(lib, name).restype = st
+        getattr(lib, name).argtypes = [P, P, P, P]
+    lib.spline_batch_prepare.restype = st
+    lib.spline_batch_prepare.argtypes = [P, P]
+    lib.spline_batch_autotune.restype = st
+    lib.spline_batch_autotune.argtypes = [P, P, P, P, P]
+    lib.spline_batch_count.restype = ctypes.c_int32
+    lib.spline_batch_count.argtypes = [P]
+    lib.spline_batch_destroy.restype = st
+    lib.spline_batch_destroy.argtypes = [P]
     lib.spline_plan_destroy.restype = st
     lib.spline_plan_destroy.argtypes = [P]
     lib.sp_release_workspace.restype = st
@@ -312,6 +332,21 @@ class Plan:
                                        gam.data_ptr() if history else None, _stream(stream)))
         return x, gam
 
+    def set_paths(self, fwd: int, adj: int):
+        """Kernel family per direction: 0 automatic, 1 strip, 2 general."""
+        _check(load().spline_plan_set_paths(self._h, int(fwd), int(adj)))
+
+    def autotune(self, coef: torch.Tensor, sino: torch.Tensor, stream=None):
+        """Time both kernel families on this data and keep the faster per
+        direction.  Returns (fwd_path, adj_path, [ms fwd strip, fwd general,
+        adj strip, adj general])."""
+        c, p = _dev_f32(coef, "coef"), _dev_f32(sino, "sino")
+        f, a = ctypes.c_int32(0), ctypes.c_int32(0)
+        ms = (ctypes.c_float * 4)()
+        _check(load().spline_plan_autotune(self._h, c.data_ptr(), p.data_ptr(), _stream(stream),
+                                           ctypes.byref(f), ctypes.byref(a), ms))
+        return f.value, a.value, list(ms)
+
     def slow_rows(self) -> int:
         """Rows read from global memory because they fell outside the staged window."""
         v = ctypes.c_int64(0)
@@ -321,6 +356,67 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             load().spline_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """spline_batch_* wrapper: independent instances projected together (one
+    CUDA graph per set of data pointers)."""
+
+    def __init__(self, grids, lines, prepare: bool = True, stream=None):
+        if len(grids) != len(lines) or not grids:
+            raise ValueError("need as many grids as line lists (>= 1)")
+        self.grids, self.lines = list(grids), list(lines)
+        self._g = (SpGrid * len(grids))(*[g.c() for g in grids])
+        self._L = (SpLines * len(lines))(*[L.c() for L in lines])
+        h = ctypes.c_void_p()
+        _check(load().spline_batch_create(len(grids), self._g, self._L, ctypes.byref(h)))
+        self._h = h
+        if prepare:
+            self.prepare(stream)
+
+    def __len__(self):
+        return len(self.grids)
+
+    def prepare(self, stream=None):
+        _check(load().spline_batch_prepare(self._h, _stream(stream)))
+
+    @staticmethod
+    def _ptrs(ts):
+        return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+    def fwd(self, coefs, sinos=None, stream=None):
+        cs = [_dev_f32(c, "coef") for c in coefs]
+        if sinos is None:
+            sinos = [torch.empty(L.m, dtype=torch.float32, device=c.device) for L, c in zip(self.lines, cs)]
+        self._keep = (cs, sinos)
+        _check(load().spline_batch_fwd(self._h, self._ptrs(cs), self._ptrs(sinos), _stream(stream)))
+        return sinos
+
+    def adj(self, sinos, coefs_out=None, stream=None):
+        ps = [_dev_f32(p, "sino") for p in sinos]
+        if coefs_out is None:
+            coefs_out = [torch.empty(g.ny, g.nx, dtype=torch.float32, device=p.device) for g, p in zip(self.grids, ps)]
+        self._keep = (ps, coefs_out)
+        _check(load().spline_batch_adj(self._h, self._ptrs(ps), self._ptrs(coefs_out), _stream(stream)))
+        return coefs_out
+
+    def autotune(self, coefs, sinos, stream=None):
+        cs = [_dev_f32(c, "coef") for c in coefs]
+        ps = [_dev_f32(p, "sino") for p in sinos]
+        paths = (ctypes.c_int32 * (2 * len(self)))()
+        _check(load().spline_batch_autotune(self._h, self._ptrs(cs), self._ptrs(ps), _stream(stream), paths))
+        return [(paths[2 * i], paths[2 * i + 1]) for i in range(len(self))]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().spline_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -150,20 +151,30 @@ int *slow_counter(const spx::GridDev &g, void *extra)
     return reinterpret_cast<int *>(static_cast<char *>(extra) + align_up(spx::strip_scratch_bytes(g)));
 }
 
-// Forward projection with the best kernel for the geometry.
-cudaError_t run_fwd(const spx::GridDev &g, const spx::LinesDev &L, const spx::LineHdr *hdr, const float *tabs,
-                    void *extra, const float *coef, float *sino, cudaStream_t s)
+// Kernel paths: strip kernels (structured geometries, degree >= 1) or the
+// general warp-per-line kernels.  kPathAuto takes the strip kernels wherever
+// they apply.
+enum KernelPath { kPathAuto = 0, kPathStrip = 1, kPathGeneral = 2 };
+
+bool use_strip(const spx::GridDev &g, const spx::LinesDev &L, void *extra, int path)
 {
-    if (extra && spx::strip_supported(g, L))
+    return path != kPathGeneral && extra && spx::strip_supported(g, L);
+}
+
+// Forward projection.
+cudaError_t run_fwd(const spx::GridDev &g, const spx::LinesDev &L, const spx::LineHdr *hdr, const float *tabs,
+                    void *extra, const float *coef, float *sino, cudaStream_t s, int path = kPathAuto)
+{
+    if (use_strip(g, L, extra, path))
         return spx::launch_fwd_strip(g, L, hdr, tabs, coef, extra, sino, slow_counter(g, extra), s);
     return spx::launch_fwd(g, hdr, tabs, L.m, coef, sino, s);
 }
 
-// Adjoint with the best kernel for the geometry (coef_out overwritten).
+// Adjoint (coef_out overwritten).
 cudaError_t run_adj(const spx::GridDev &g, const spx::LinesDev &L, const spx::LineHdr *hdr, const float *tabs,
-                    void *extra, const float *sino, float *coef_out, cudaStream_t s)
+                    void *extra, const float *sino, float *coef_out, cudaStream_t s, int path = kPathAuto)
 {
-    if (extra && spx::strip_supported(g, L))
+    if (use_strip(g, L, extra, path))
         return spx::launch_adj_strip(g, L, hdr, tabs, sino, extra, coef_out, slow_counter(g, extra), s);
     return spx::launch_adj(g, hdr, tabs, L.m, sino, coef_out, s);
 }
@@ -312,6 +323,7 @@ struct sp_plan {
     bool prepared;
     void *cg_ws;       // CGLS vectors and scalars, allocated on first use
     size_t cg_bytes;
+    int path_fwd, path_adj;   // KernelPath of each direction
 };
 
 sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan **plan)
@@ -349,6 +361,7 @@ sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan
     p->prepared = false;
     p->cg_ws = nullptr;
     p->cg_bytes = 0;
+    p->path_fwd = p->path_adj = kPathAuto;
     if (p->extra) {
         e = cudaMemset(slow_counter(g, p->extra), 0, sizeof(int));
         if (e != cudaSuccess) {
@@ -383,7 +396,7 @@ sp_status spline_plan_fwd(const sp_plan *plan, const float *coef, float *sino, v
     if (plan->L.m == 0) return SP_OK;
     if (!coef || !sino) return fail(SP_EINVAL, "coef/sino pointers are NULL");
     cudaError_t e = run_fwd(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, coef, sino,
-                            static_cast<cudaStream_t>(stream));
+                            static_cast<cudaStream_t>(stream), plan->path_fwd);
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "forward projection");
 }
 
@@ -395,7 +408,7 @@ sp_status spline_plan_adj(const sp_plan *plan, const float *sino, float *coef_ou
     if (!coef_out) return fail(SP_EINVAL, "coef_out pointer is NULL");
     if (plan->L.m > 0 && !sino) return fail(SP_EINVAL, "sino pointer is NULL");
     cudaError_t e = run_adj(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, sino, coef_out,
-                            static_cast<cudaStream_t>(stream));
+                            static_cast<cudaStream_t>(stream), plan->path_adj);
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "adjoint projection");
 }
 
@@ -403,12 +416,12 @@ namespace {
 cudaError_t plan_fwd_cb(void *ctx, const float *coef, float *sino, cudaStream_t s)
 {
     const sp_plan *p = static_cast<const sp_plan *>(ctx);
-    return run_fwd(p->g, p->L, p->hdr, p->tabs, p->extra, coef, sino, s);
+    return run_fwd(p->g, p->L, p->hdr, p->tabs, p->extra, coef, sino, s, p->path_fwd);
 }
 cudaError_t plan_adj_cb(void *ctx, const float *sino, float *coef_out, cudaStream_t s)
 {
     const sp_plan *p = static_cast<const sp_plan *>(ctx);
-    return run_adj(p->g, p->L, p->hdr, p->tabs, p->extra, sino, coef_out, s);
+    return run_adj(p->g, p->L, p->hdr, p->tabs, p->extra, sino, coef_out, s, p->path_adj);
 }
 }  // namespace
 
@@ -445,6 +458,284 @@ sp_status spline_plan_cgls(sp_plan *plan, const float *b, float *x, int32_t iter
 }
 
 int64_t spline_plan_lines(const sp_plan *plan) { return plan ? plan->L.m : -1; }
+
+}  // extern "C"
+
+namespace {
+// Mean device time of `reps` runs of f on stream s (after one untimed run).
+template <typename F>
+cudaError_t time_runs(F f, int reps, cudaStream_t s, float *ms)
+{
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return e; }
+    if ((e = f()) == cudaSuccess && (e = cudaEventRecord(a, s)) == cudaSuccess) {
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = f();
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+        if (e == cudaSuccess) *ms /= (float)reps;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e;
+}
+}  // namespace
+
+extern "C" {
+
+sp_status spline_plan_set_paths(sp_plan *plan, int32_t fwd_path, int32_t adj_path)
+{
+    g_err.clear();
+    if (!plan) return fail(SP_EINVAL, "plan is NULL");
+    if (fwd_path < 0 || fwd_path > 2 || adj_path < 0 || adj_path > 2) return fail(SP_EINVAL, "path must be 0, 1 or 2");
+    plan->path_fwd = fwd_path;
+    plan->path_adj = adj_path;
+    return SP_OK;
+}
+
+sp_status spline_plan_autotune(sp_plan *plan, const float *coef, const float *sino, void *stream,
+                               int32_t *fwd_path, int32_t *adj_path, float *ms_out)
+{
+    g_err.clear();
+    if (!plan) return fail(SP_EINVAL, "plan is NULL");
+    if (!plan->prepared) return fail(SP_EINVAL, "plan not prepared");
+    const int64_t n = (int64_t)plan->g.nx * plan->g.ny, m = plan->L.m;
+    if (m > 0 && (!coef || !sino)) return fail(SP_EINVAL, "coef/sino pointers are NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool both = plan->extra && spx::strip_supported(plan->g, plan->L) && m > 0;
+    float t[4] = {0.f, 0.f, 0.f, 0.f};   // fwd strip, fwd general, adj strip, adj general
+    int bf = both ? kPathStrip : kPathGeneral, ba = bf;
+    if (both) {
+        float *tmp_s = nullptr, *tmp_c = nullptr;
+        cudaError_t e = cudaMalloc(&tmp_s, sizeof(float) * (size_t)m);
+        if (e == cudaSuccess) e = cudaMalloc(&tmp_c, sizeof(float) * (size_t)n);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            const int path = (k & 1) ? kPathGeneral : kPathStrip;
+            if (k < 2)
+                e = time_runs([&] { return run_fwd(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, coef, tmp_s, s, path); },
+                              3, s, &t[k]);
+            else
+                e = time_runs([&] { return run_adj(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, sino, tmp_c, s, path); },
+                              3, s, &t[k]);
+        }
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (tmp_s) cudaFree(tmp_s);
+        if (tmp_c) cudaFree(tmp_c);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) return cuda_fail(e, "autotune");
+        bf = t[0] <= t[1] ? kPathStrip : kPathGeneral;
+        ba = t[2] <= t[3] ? kPathStrip : kPathGeneral;
+    }
+    plan->path_fwd = bf;
+    plan->path_adj = ba;
+    if (fwd_path) *fwd_path = bf;
+    if (adj_path) *adj_path = ba;
+    if (ms_out) for (int k = 0; k < 4; ++k) ms_out[k] = t[k];
+    return SP_OK;
+}
+
+// ------------------------------------------------------------------ batches
+// A batch is a set of plans run together: each call forks the instances over
+// internal streams and joins them back on the caller's stream, recorded once
+// as a CUDA graph per set of data pointers and replayed afterwards.
+}  // extern "C"
+
+namespace {
+constexpr int kBatchStreams = 8;
+
+struct GraphCache {
+    std::vector<const void *> key;
+    cudaGraphExec_t exec = nullptr;
+    void clear()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key.clear();
+    }
+};
+}  // namespace
+
+extern "C" {
+
+struct sp_batch {
+    std::vector<sp_plan *> plans;
+    cudaStream_t cap = nullptr;                 // capture origin
+    cudaStream_t streams[kBatchStreams] = {};
+    cudaEvent_t fork = nullptr, join[kBatchStreams] = {};
+    GraphCache gfwd, gadj;
+};
+
+}  // extern "C"
+
+namespace {
+void batch_free(sp_batch *b)
+{
+    if (!b) return;
+    b->gfwd.clear();
+    b->gadj.clear();
+    for (int k = 0; k < kBatchStreams; ++k) {
+        if (b->streams[k]) cudaStreamDestroy(b->streams[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (sp_plan *p : b->plans) spline_plan_destroy(p);
+    delete b;
+}
+
+// Fork the instances over the internal streams from `origin`, run op(i, s)
+// for instance i, and join back on `origin`.
+template <typename Op>
+cudaError_t fork_join(sp_batch *b, cudaStream_t origin, Op op)
+{
+    cudaError_t e = cudaEventRecord(b->fork, origin);
+    for (int k = 0; k < kBatchStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->streams[k], b->fork, 0);
+    for (size_t i = 0; i < b->plans.size() && e == cudaSuccess; ++i) e = op(i, b->streams[i % kBatchStreams]);
+    for (int k = 0; k < kBatchStreams && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->join[k], b->streams[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, b->join[k], 0);
+    }
+    return e;
+}
+
+// Replay the cached graph for these pointers, or capture a new one.
+template <typename Op>
+cudaError_t run_graph(sp_batch *b, GraphCache &gc, const std::vector<const void *> &key, cudaStream_t s, Op op)
+{
+    if (!gc.exec || gc.key != key) {
+        gc.clear();
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaError_t eop = fork_join(b, b->cap, op);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(b->cap, &graph);
+        if (eop != cudaSuccess) e = eop;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gc.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            gc.exec = nullptr;
+            return e;
+        }
+        gc.key = key;
+    }
+    return cudaGraphLaunch(gc.exec, s);
+}
+}  // namespace
+
+extern "C" {
+
+sp_status spline_batch_create(int32_t count, const sp_grid *grids, const sp_lines *lines, sp_batch **batch)
+{
+    g_err.clear();
+    if (!batch) return fail(SP_EINVAL, "batch is NULL");
+    *batch = nullptr;
+    if (count < 1) return fail(SP_EINVAL, "count must be >= 1");
+    if (!grids || !lines) return fail(SP_EINVAL, "grids/lines are NULL");
+    sp_batch *b = new sp_batch;
+    for (int32_t i = 0; i < count; ++i) {
+        sp_plan *p = nullptr;
+        sp_status st = spline_plan_create(grids + i, lines + i, &p);
+        if (st != SP_OK) {
+            std::string msg = "instance " + std::to_string(i) + ": " + g_err;
+            batch_free(b);
+            return fail(st, msg);
+        }
+        b->plans.push_back(p);
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int k = 0; k < kBatchStreams && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, "batch streams");
+    }
+    *batch = b;
+    return SP_OK;
+}
+
+sp_status spline_batch_prepare(sp_batch *batch, void *stream)
+{
+    g_err.clear();
+    if (!batch) return fail(SP_EINVAL, "batch is NULL");
+    sp_status st = SP_OK;
+    cudaError_t e = fork_join(batch, static_cast<cudaStream_t>(stream), [&](size_t i, cudaStream_t s) {
+        st = spline_plan_prepare(batch->plans[i], s);
+        return st == SP_OK ? cudaSuccess : cudaErrorUnknown;
+    });
+    if (st != SP_OK) return st;
+    return e == cudaSuccess ? SP_OK : cuda_fail(e, "batch prepare");
+}
+
+sp_status spline_batch_fwd(sp_batch *batch, const float *const *coef, float *const *sino, void *stream)
+{
+    g_err.clear();
+    if (!batch || !coef || !sino) return fail(SP_EINVAL, "NULL argument");
+    std::vector<const void *> key;
+    for (size_t i = 0; i < batch->plans.size(); ++i) {
+        const sp_plan *p = batch->plans[i];
+        if (!p->prepared) return fail(SP_EINVAL, "instance " + std::to_string(i) + " not prepared");
+        if (p->L.m > 0 && (!coef[i] || !sino[i])) return fail(SP_EINVAL, "NULL pointer of instance " + std::to_string(i));
+        key.push_back(coef[i]);
+        key.push_back(sino[i]);
+    }
+    cudaError_t e = run_graph(batch, batch->gfwd, key, static_cast<cudaStream_t>(stream), [&](size_t i, cudaStream_t s) {
+        const sp_plan *p = batch->plans[i];
+        if (p->L.m == 0) return cudaSuccess;
+        return run_fwd(p->g, p->L, p->hdr, p->tabs, p->extra, coef[i], sino[i], s, p->path_fwd);
+    });
+    return e == cudaSuccess ? SP_OK : cuda_fail(e, "batch forward");
+}
+
+sp_status spline_batch_adj(sp_batch *batch, const float *const *sino, float *const *coef_out, void *stream)
+{
+    g_err.clear();
+    if (!batch || !sino || !coef_out) return fail(SP_EINVAL, "NULL argument");
+    std::vector<const void *> key;
+    for (size_t i = 0; i < batch->plans.size(); ++i) {
+        const sp_plan *p = batch->plans[i];
+        if (!p->prepared) return fail(SP_EINVAL, "instance " + std::to_string(i) + " not prepared");
+        if (!coef_out[i] || (p->L.m > 0 && !sino[i])) return fail(SP_EINVAL, "NULL pointer of instance " + std::to_string(i));
+        key.push_back(sino[i]);
+        key.push_back(coef_out[i]);
+    }
+    cudaError_t e = run_graph(batch, batch->gadj, key, static_cast<cudaStream_t>(stream), [&](size_t i, cudaStream_t s) {
+        const sp_plan *p = batch->plans[i];
+        return run_adj(p->g, p->L, p->hdr, p->tabs, p->extra, sino[i], coef_out[i], s, p->path_adj);
+    });
+    return e == cudaSuccess ? SP_OK : cuda_fail(e, "batch adjoint");
+}
+
+sp_status spline_batch_autotune(sp_batch *batch, const float *const *coef, const float *const *sino, void *stream,
+                                int32_t *paths)
+{
+    g_err.clear();
+    if (!batch || !coef || !sino) return fail(SP_EINVAL, "NULL argument");
+    for (size_t i = 0; i < batch->plans.size(); ++i) {
+        int32_t f = 0, a = 0;
+        sp_status st = spline_plan_autotune(batch->plans[i], coef[i], sino[i], stream, &f, &a, nullptr);
+        if (st != SP_OK) return fail(st, "instance " + std::to_string(i) + ": " + g_err);
+        if (paths) { paths[2 * i] = f; paths[2 * i + 1] = a; }
+    }
+    batch->gfwd.clear();
+    batch->gadj.clear();
+    return SP_OK;
+}
+
+int32_t spline_batch_count(const sp_batch *batch) { return batch ? (int32_t)batch->plans.size() : -1; }
+
+sp_status spline_batch_destroy(sp_batch *batch)
+{
+    g_err.clear();
+    if (!batch) return SP_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    batch_free(batch);
+    return e == cudaSuccess ? SP_OK : cuda_fail(e, "cudaDeviceSynchronize");
+}
 
 sp_status spline_plan_stats(const sp_plan *plan, int64_t *slow_rows)
 {

@@ -1,0 +1,104 @@
+"""Batches of uneven instances (one CUDA graph per set of data pointers) and
+the autotuner's kernel choice: the batch gives what each instance's own plan
+gives, replays and re-records correctly, and every kernel choice keeps the
+oracle parity bar (relative L2 <= 1e-5)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from _geom import device_lines, oracle_lines, rel_l2
+
+torch = pytest.importorskip("torch")
+sp = pytest.importorskip("paper_2503_20907_gb300")
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _instances():
+    ws = [workloads.batch_instance(i, 0.12) for i in range(12)]
+    # plus a box-spline fan instance
+    base = workloads.crop_workload(workloads.workload("fan512_cubic"), 40)
+    return ws, base
+
+
+@pytest.fixture(scope="module")
+def batch_setup():
+    ws, box = _instances()
+    grids = [sp.Grid(w.n, w.n, w.degree, w.h) for w in ws] + [sp.Grid(box.n, box.n, 1, box.h, basis=sp.BASIS_BOX3)]
+    lines = [device_lines(w.geometry, DEV) for w in ws] + [device_lines(box.geometry, DEV)]
+    coefs = [torch.from_numpy(w.coef).to(DEV) for w in ws] + [torch.from_numpy(box.coef).to(DEV)]
+    batch = sp.Batch(grids, lines)
+    plans = [sp.Plan(g, L) for g, L in zip(grids, lines)]
+    return ws + [box], grids, lines, coefs, batch, plans
+
+
+def test_batch_matches_plans_and_replays(batch_setup):
+    ws, grids, lines, coefs, batch, plans = batch_setup
+    sinos = batch.fwd(coefs)
+    torch.cuda.synchronize()
+    for s, p, c in zip(sinos, plans, coefs):
+        assert torch.equal(s, p.fwd(c))          # same kernels, deterministic forward
+    again = batch.fwd(coefs, sinos=[torch.empty_like(s) for s in sinos])   # new pointers: re-recorded
+    for a, b in zip(again, sinos):
+        assert torch.equal(a, b)
+    same = batch.fwd(coefs, sinos=again)        # same pointers: replayed graph
+    for a, b in zip(same, sinos):
+        assert torch.equal(a, b)
+    backs = batch.adj(sinos)
+    for bk, p, s in zip(backs, plans, sinos):
+        ref = p.adj(s)
+        assert float((bk - ref).norm() / ref.norm().clamp_min(1e-30)) < 1e-6
+
+
+def test_batch_instances_match_oracle(batch_setup):
+    ws, grids, lines, coefs, batch, plans = batch_setup
+    sinos = batch.fwd(coefs)
+    for k in (0, 2, 7, len(ws) - 1):
+        w, g = ws[k], grids[k]
+        og = oracle.Grid(w.n, w.n, g.degree, w.h, basis=g.basis)
+        th, yy = oracle_lines(w.geometry)
+        idx = np.arange(th.size) if th.size <= 3000 else np.random.default_rng(k).choice(th.size, 3000, replace=False)
+        ref = oracle.forward(og, w.coef, th[idx], yy[idx])
+        assert rel_l2(sinos[k].cpu().numpy()[idx], ref) < 1e-5
+
+
+def test_autotune_choices_keep_parity(batch_setup):
+    ws, grids, lines, coefs, batch, plans = batch_setup
+    sinos = [p.fwd(c) for p, c in zip(plans, coefs)]
+    paths = batch.autotune(coefs, sinos)
+    assert len(paths) == len(ws)
+    for (f, a), L, g in zip(paths, lines, grids):
+        assert f in (1, 2) and a in (1, 2)
+        if L.kind == sp._lib.KIND_POINTS or g.degree == 0:
+            assert (f, a) == (2, 2)               # strip kernels do not apply
+    out = batch.fwd(coefs)
+    back = batch.adj(sinos)
+    for k in (1, 3, len(ws) - 1):
+        w, g = ws[k], grids[k]
+        og = oracle.Grid(w.n, w.n, g.degree, w.h, basis=g.basis)
+        th, yy = oracle_lines(w.geometry)
+        assert rel_l2(out[k].cpu().numpy(), oracle.forward(og, w.coef, th, yy)) < 1e-5
+        assert rel_l2(back[k].cpu().numpy(), oracle.adjoint(og, sinos[k].cpu().numpy(), th, yy)) < 1e-5
+
+
+def test_general_and_strip_kernels_agree(batch_setup):
+    ws, grids, lines, coefs, batch, plans = batch_setup
+    for p, c, L, g in zip(plans, coefs, lines, grids):
+        if L.kind not in (sp._lib.KIND_PARALLEL, sp._lib.KIND_FAN) or g.degree == 0:
+            continue
+        p.set_paths(1, 1)
+        s1 = p.fwd(c)
+        b1 = p.adj(s1)
+        p.set_paths(2, 2)
+        s2 = p.fwd(c)
+        b2 = p.adj(s1)
+        p.set_paths(0, 0)
+        assert float((s1 - s2).norm() / s2.norm()) < 1e-6
+        assert float((b1 - b2).norm() / b2.norm()) < 1e-6
+
+
+def test_batch_invalid():
+    with pytest.raises(sp.SplineError):
+        sp.Batch([sp.Grid(8, 8, 5)], [sp.Lines.theta_y(torch.zeros(3, device=DEV), torch.zeros(3, device=DEV))])

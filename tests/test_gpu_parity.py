@@ -230,3 +230,19 @@ def test_strip_windows_cover_every_run(name):
     plan.fwd(torch.from_numpy(wl.coef).to(DEV))
     assert plan.slow_rows() == 0
     plan.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_diagonal_and_axis_lines_through_nodes(n):
+    # directions where sin and cos round to the same float (or one vanishes),
+    # on lines through nodes: rows step by the exact |kappa|, the tables use
+    # the float a
+    N = 24
+    g, og = _grid(N, n)
+    base = [0.0, math.pi / 4, math.pi / 2, 3 * math.pi / 4, math.pi, 5 * math.pi / 4]
+    th = np.repeat(np.array(base, dtype=np.float32), 33)
+    y = np.tile(np.linspace(-16.0, 16.0, 33), len(base)).astype(np.float32)
+    coef = workloads.ellipse_phantom(N, 6, 43, radius=8.0, axes=(2.0, 7.0))
+    lines = sp.Lines.theta_y(torch.from_numpy(th).to(DEV), torch.from_numpy(y).to(DEV))
+    sino = sp.spline_project_fwd(g, torch.from_numpy(coef).to(DEV), lines).cpu().numpy()
+    assert rel_l2(sino, oracle.forward(og, coef, th.astype(np.float64), y.astype(np.float64))) < TOL

@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "ellipse_phantom", "Geometry", "Workload", "workload", "crop_workload",
-    "random_lines_circle", "poisson_counts", "transmission_data",
+    "random_lines_circle", "poisson_counts", "transmission_data", "batch_instance",
 ]
 
 
@@ -187,3 +187,33 @@ def transmission_data(expected: np.ndarray, seed: int, peak: float = 3.0, I0: fl
     kappa = peak / top if top > 0 else 1.0
     counts = poisson_counts(I0 * np.exp(-kappa * e), seed)
     return -np.log(np.maximum(counts, 1.0) / I0) / kappa, kappa
+
+
+def batch_instance(i: int, scale: float = 1.0) -> Workload:
+    """Instance i of the uneven batch (seed 1000 + i).
+
+    N = round(exp U[ln 128, ln 1024] * scale), degree U{0..3}; one instance in
+    eight is a free line list of M ~ U[1e5, 1e6] * scale^2 chords with both
+    endpoints at angles U[0, 2 pi) on the circle of radius 0.75 N; the others
+    are parallel or fan beams (probability 1/2 each) with U{180..1440} * scale
+    views and round(1.5 N) bins of width 1 (fan: dso = 1000 N/512,
+    dod = 500 N/512).  The phantom has 10 ellipses scaled to the grid."""
+    rng = np.random.default_rng(1000 + i)
+    n = max(16, int(round(math.exp(rng.uniform(math.log(128), math.log(1024))) * scale)))
+    degree = int(rng.integers(0, 4))
+    s = n / 64.0
+    coef = ellipse_phantom(n, 10, 1000 + i, radius=24.0 * s, axes=(2.0 * s, 16.0 * s))
+    if i % 8 == 7:
+        m = max(1000, int(rng.uniform(1e5, 1e6) * scale * scale))
+        src, dst = random_lines_circle(m, 0.75 * n, 1000 + i)
+        geo = Geometry("points", src=src, dst=dst)
+    else:
+        n_view = max(8, int(round(rng.integers(180, 1441) * scale)))
+        n_det = int(round(1.5 * n))
+        if rng.uniform() < 0.5:
+            geo = Geometry("parallel", view_angle=_angles(n_view, math.pi), n_det=n_det,
+                           det0=-0.5 * (n_det - 1), ddet=1.0)
+        else:
+            geo = Geometry("fan", view_angle=_angles(n_view, 2.0 * math.pi), n_det=n_det,
+                           det0=-0.5 * (n_det - 1), ddet=1.0, dso=1000.0 * n / 512.0, dod=500.0 * n / 512.0)
+    return Workload(f"batch{i}", n, degree, 1.0, geo, coef, 1000 + i)
