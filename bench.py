@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true", help="skip the CGLS timing (not part of the step)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch timing (not part of the step)")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="size scale of the uneven batch")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="fan512_cubic (the benchmark) or fan256_cubic (small profiling case)")
     return ap.parse_args()
@@ -182,6 +184,52 @@ def run_reference(args, rank, ws):
 
 
 # ------------------------------------------------------------------ GPU
+def run_batch(args, sp, dev, stream, count=64):
+    """The uneven batch (64 seeded instances, one CUDA graph per direction),
+    autotuned; lines per second over forward + adjoint of all instances."""
+    import torch
+    import workloads
+
+    ws_ = [workloads.batch_instance(i, args.batch_scale) for i in range(count)]
+    grids, lines, coefs = [], [], []
+    for w in ws_:
+        geo = w.geometry
+        grids.append(sp.Grid(w.n, w.n, w.degree, w.h))
+        if geo.kind == "points":
+            lines.append(sp.Lines.points(torch.from_numpy(geo.src).to(dev), torch.from_numpy(geo.dst).to(dev)))
+        elif geo.kind == "parallel":
+            lines.append(sp.Lines.parallel(torch.from_numpy(geo.view_angle).to(dev), geo.n_det, geo.det0, geo.ddet))
+        else:
+            lines.append(sp.Lines.fan(torch.from_numpy(geo.view_angle).to(dev), geo.dso, geo.dod, geo.n_det,
+                                      geo.det0, geo.ddet))
+        coefs.append(torch.from_numpy(w.coef).to(dev))
+    batch = sp.Batch(grids, lines)
+    sinos = batch.fwd(coefs)
+    backs = batch.adj(sinos)
+    paths = batch.autotune(coefs, sinos)
+    for _ in range(3):
+        batch.fwd(coefs, sinos)
+        batch.adj(sinos, backs)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    a.record(stream)
+    for _ in range(reps):
+        batch.fwd(coefs, sinos)
+        batch.adj(sinos, backs)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    m_tot = sum(L.m for L in lines)
+    out = {"workload": f"{count} seeded uneven instances (sizes 128..1024 x {args.batch_scale:g}, degrees 0..3, "
+                       "parallel/fan views, 1 in 8 a free line list)",
+           "lines": m_tot, "ms_fwd_adj": ms, "mrays_per_s": m_tot / (ms / 1000.0) / 1e6,
+           "strip_fwd": sum(1 for f, _ in paths if f == 1), "strip_adj": sum(1 for _, x in paths if x == 1),
+           "graphs": "one CUDA graph per direction, replayed"}
+    batch.close()
+    return out
+
+
 def run_ours(args, rank, ws, local):
     import numpy as np
     import torch
@@ -292,6 +340,8 @@ def run_ours(args, rank, ws, local):
                                                          None),
               "kernels_per_iter": 8}
 
+    batch = None if args.no_batch else run_batch(args, sp, dev, stream)
+
     if rank != 0:
         return
     value = ws * M * args.steps / tmax / 1e6
@@ -327,6 +377,8 @@ def run_ours(args, rank, ws, local):
     }
     if cg is not None:
         line["cg"] = cg
+    if batch is not None:
+        line["batch"] = batch
     if ws == 1 and not args.no_cpu_baseline and wl.name == WORKLOAD:
         cb = oracle_sample(wl)
         cb.pop("seconds", None)
