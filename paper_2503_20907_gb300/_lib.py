@@ -47,7 +47,8 @@ EXPORTED = ("sp_lines_count", "spline_project_fwd", "spline_project_adj", "splin
             "spline_plan_adj", "spline_plan_lines", "spline_plan_destroy", "spline_plan_stats",
             "spline_project_fwd_noalloc", "spline_plan_cgls", "spline_plan_set_paths",
             "spline_plan_autotune", "spline_batch_create", "spline_batch_prepare", "spline_batch_fwd",
-            "spline_batch_adj", "spline_batch_autotune", "spline_batch_count", "spline_batch_destroy")
+            "spline_batch_adj", "spline_batch_autotune", "spline_batch_count", "spline_batch_destroy",
+            "sp_conv3x3_fwd", "sp_conv3x3_bwd_data", "sp_conv3x3_bwd_weight", "sp_conv3x3_flip_weights")
 
 
 def load(build_if_stale: bool = True) -> ctypes.CDLL:
@@ -105,6 +106,15 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
     lib.spline_batch_count.argtypes = [P]
     lib.spline_batch_destroy.restype = st
     lib.spline_batch_destroy.argtypes = [P]
+    i32 = ctypes.c_int32
+    lib.sp_conv3x3_fwd.restype = st
+    lib.sp_conv3x3_fwd.argtypes = [i32, i32, i32, i32, i32, P, P, P, i32, P, P]
+    lib.sp_conv3x3_bwd_data.restype = st
+    lib.sp_conv3x3_bwd_data.argtypes = [i32, i32, i32, i32, i32, P, P, P, P, P]
+    lib.sp_conv3x3_bwd_weight.restype = st
+    lib.sp_conv3x3_bwd_weight.argtypes = [i32, i32, i32, i32, i32, P, P, P, P, P]
+    lib.sp_conv3x3_flip_weights.restype = st
+    lib.sp_conv3x3_flip_weights.argtypes = [i32, i32, P, P, P]
     lib.spline_plan_destroy.restype = st
     lib.spline_plan_destroy.argtypes = [P]
     lib.sp_release_workspace.restype = st

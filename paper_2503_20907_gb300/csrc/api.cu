@@ -207,6 +207,7 @@ namespace spx {
 sp_status check_grid_for(const sp_grid *g, GridDev *out) { return check_grid(g, out); }
 sp_status check_lines_for(const sp_lines *L, LinesDev *out) { return check_lines(L, out); }
 sp_status record_error(sp_status st, const std::string &msg) { return fail(st, msg); }
+sp_status record_error(sp_status st, const char *msg) { return fail(st, std::string(msg)); }
 void clear_error() { g_err.clear(); }
 }  // namespace spx
 

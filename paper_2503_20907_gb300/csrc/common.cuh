@@ -261,6 +261,11 @@ cudaError_t launch_footprint_eval(const GridDev &g, int64_t count, const float *
                                   float *out, float *scratch, cudaStream_t s);
 
 
+// Argument errors and the thread-local message of the C ABI (api.cu), for the
+// entry points defined in other translation units.
+sp_status record_error(sp_status st, const char *msg);
+void clear_error();
+
 // CGLS (cg.cu).  The projector is passed as callbacks so that cg.cu does not
 // depend on how a plan runs its projections.
 struct CgOps {

@@ -1,0 +1,366 @@
+// 3x3 convolution layers of the warm-start network (no paper counterpart):
+// stride 1, zero padding 1, NHWC, BF16 activations and weights, FP32
+// accumulation.
+//
+//   forward, 32 -> 32 channels: implicit GEMM on the tensor cores
+//     (mma.sync m16n8k16, BF16 in, FP32 accumulate).  A CTA takes 64 pixels
+//     of one image row; the three input rows it needs and the weights are
+//     staged in shared memory with padded strides (no bank conflicts on the
+//     fragment loads).  Epilogue: bias, optional ReLU, BF16 store.
+//   forward, 1 -> 32 and 32 -> 1: CUDA cores, thread per pixel.
+//   gradients (training): CUDA cores in FP32 with BF16 activations and
+//     weights read as stored; the input gradient can be gated by the ReLU of
+//     the layer below (x > 0).
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+
+#include "common.cuh"
+#include "../../include/warmstart_conv.h"
+
+namespace spx {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kC = 32;              // channels of the inner layers
+constexpr int kTileW = 64;          // pixels of one CTA (4 warps x 16)
+constexpr int kXStride = 40;        // bf16 per staged pixel (32 + 8: conflict-free fragment loads)
+constexpr int kWStride = 9 * kC + 8;   // bf16 per staged output channel
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// y = conv(x) + bias (ReLU optional), 32 -> 32 channels.
+__global__ void __launch_bounds__(128) conv32_fwd_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
+                                                         const float *__restrict__ bias, bf16 *__restrict__ y,
+                                                         int B, int H, int W, int relu)
+{
+    __shared__ __align__(16) bf16 xs[3][kTileW + 2][kXStride];
+    __shared__ __align__(16) bf16 ws[kC][kWStride];
+    const int tiles_w = (W + kTileW - 1) / kTileW;
+    const int tw = blockIdx.x % tiles_w;
+    const int h = (blockIdx.x / tiles_w) % H;
+    const int b = blockIdx.x / (tiles_w * H);
+    const int w0 = tw * kTileW;
+    // weights: 32 x 288 bf16, 16-byte chunks (36 per channel)
+    for (int i = threadIdx.x; i < kC * 36; i += 128) {
+        const int o = i / 36, c = i - o * 36;
+        *reinterpret_cast<uint4 *>(&ws[o][c * 8]) = *reinterpret_cast<const uint4 *>(w + (size_t)o * 9 * kC + c * 8);
+    }
+    // input rows h-1..h+1, pixels w0-1..w0+64, 16-byte chunks of 8 channels
+    for (int i = threadIdx.x; i < 3 * (kTileW + 2) * 4; i += 128) {
+        const int r = i / ((kTileW + 2) * 4), rem = i - r * (kTileW + 2) * 4;
+        const int p = rem >> 2, c = rem & 3;
+        const int hh = h + r - 1, ww = w0 + p - 1;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (hh >= 0 && hh < H && ww >= 0 && ww < W)
+            v = *reinterpret_cast<const uint4 *>(x + (((size_t)b * H + hh) * W + ww) * kC + c * 8);
+        *reinterpret_cast<uint4 *>(&xs[r][p][c * 8]) = v;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int pb = warp * 16;   // first pixel of the warp in the tile
+    float acc[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[nt][k] = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+#pragma unroll
+        for (int cb = 0; cb < 2; ++cb) {
+            const int c0 = cb * 16 + 2 * t;
+            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(&xs[ky][pb + g + kx][c0]);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(&xs[ky][pb + g + 8 + kx][c0]);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(&xs[ky][pb + g + kx][c0 + 8]);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(&xs[ky][pb + g + 8 + kx][c0 + 8]);
+            const int k0 = tap * kC + cb * 16 + 2 * t;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&ws[nt * 8 + g][k0]);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&ws[nt * 8 + g][k0 + 8]);
+                mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    // epilogue: (pixel pb+g, channels 2t, 2t+1) and (pixel pb+g+8, same)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        const int o = nt * 8 + 2 * t;
+        const float b0 = bias ? bias[o] : 0.f, b1 = bias ? bias[o + 1] : 0.f;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int ww = w0 + pb + g + 8 * half;
+            if (ww >= W) continue;
+            float v0 = acc[nt][2 * half] + b0, v1 = acc[nt][2 * half + 1] + b1;
+            if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+            *reinterpret_cast<__nv_bfloat162 *>(y + (((size_t)b * H + h) * W + ww) * kC + o) =
+                __floats2bfloat162_rn(v0, v1);
+        }
+    }
+}
+
+__device__ __forceinline__ float ld_act(const bf16 *p) { return __bfloat162float(*p); }
+
+// Forward on CUDA cores for cin = 1 (y bf16 [.., 32]) or cout = 1 (y float [..]).
+__global__ void conv_edge_fwd_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
+                                     const float *__restrict__ bias, void *y, int B, int H, int W, int cin,
+                                     int cout, int relu)
+{
+    __shared__ float wsh[9 * kC];
+    for (int i = threadIdx.x; i < 9 * kC; i += blockDim.x) wsh[i] = __bfloat162float(w[i]);
+    __syncthreads();
+    const int64_t n = (int64_t)B * H * W;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int ww = (int)(p % W), hh = (int)((p / W) % H);
+        const int64_t bb = p / ((int64_t)W * H);
+        if (cin == 1) {
+            float acc[kC];
+#pragma unroll
+            for (int o = 0; o < kC; ++o) acc[o] = bias ? bias[o] : 0.f;
+            for (int tap = 0; tap < 9; ++tap) {
+                const int y0 = hh + tap / 3 - 1, x0 = ww + tap % 3 - 1;
+                if (y0 < 0 || y0 >= H || x0 < 0 || x0 >= W) continue;
+                const float v = ld_act(x + (bb * H + y0) * W + x0);
+#pragma unroll
+                for (int o = 0; o < kC; ++o) acc[o] = __fmaf_rn(v, wsh[o * 9 + tap], acc[o]);
+            }
+            bf16 *out = static_cast<bf16 *>(y) + p * kC;
+#pragma unroll
+            for (int o = 0; o < kC; o += 2) {
+                float v0 = acc[o], v1 = acc[o + 1];
+                if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                *reinterpret_cast<__nv_bfloat162 *>(out + o) = __floats2bfloat162_rn(v0, v1);
+            }
+        } else {
+            float acc = bias ? bias[0] : 0.f;
+            for (int tap = 0; tap < 9; ++tap) {
+                const int y0 = hh + tap / 3 - 1, x0 = ww + tap % 3 - 1;
+                if (y0 < 0 || y0 >= H || x0 < 0 || x0 >= W) continue;
+                const bf16 *xp = x + ((bb * H + y0) * W + x0) * kC;
+#pragma unroll
+                for (int i = 0; i < kC; ++i) acc = __fmaf_rn(ld_act(xp + i), wsh[tap * kC + i], acc);
+            }
+            if (relu) acc = fmaxf(acc, 0.f);
+            static_cast<float *>(y)[p] = acc;
+        }
+    }
+}
+
+// dx[p, i] = sum_{tap, o} g[p - off(tap), o] W[o, tap, i], gated by x_gate[p, i] > 0.
+template <int CIN, int COUT>
+__global__ void conv_dgrad_kernel(const float *__restrict__ g, const bf16 *__restrict__ w,
+                                  const bf16 *__restrict__ gate, float *__restrict__ dx, int B, int H, int W)
+{
+    __shared__ float wsh[COUT * 9 * CIN];
+    for (int i = threadIdx.x; i < COUT * 9 * CIN; i += blockDim.x) wsh[i] = __bfloat162float(w[i]);
+    __syncthreads();
+    const int64_t n = (int64_t)B * H * W;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int ww = (int)(p % W), hh = (int)((p / W) % H);
+        const int64_t bb = p / ((int64_t)W * H);
+        float acc[CIN];
+#pragma unroll
+        for (int i = 0; i < CIN; ++i) acc[i] = 0.f;
+        for (int tap = 0; tap < 9; ++tap) {
+            const int y0 = hh - (tap / 3 - 1), x0 = ww - (tap % 3 - 1);
+            if (y0 < 0 || y0 >= H || x0 < 0 || x0 >= W) continue;
+            const float *gp = g + ((bb * H + y0) * W + x0) * COUT;
+#pragma unroll 4
+            for (int o = 0; o < COUT; ++o) {
+                const float gv = gp[o];
+                const float *wr = wsh + (o * 9 + tap) * CIN;
+#pragma unroll
+                for (int i = 0; i < CIN; ++i) acc[i] = __fmaf_rn(gv, wr[i], acc[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < CIN; ++i) {
+            float v = acc[i];
+            if (gate && !(__bfloat162float(gate[p * CIN + i]) > 0.f)) v = 0.f;
+            dx[p * CIN + i] = v;
+        }
+    }
+}
+
+// dW[o, tap, i] += sum_p g[p, o] x[p + off(tap), i]; dbias[o] += sum_p g[p, o].
+// A CTA takes `rows` image rows (over B*H) one at a time, with the row of g
+// (FP32) and the three rows of x it meets (BF16) staged in shared memory.
+// Each thread owns a block of OB x IB outputs of one tap (OB = min(cout, 4),
+// IB = min(cin, 4)); the bias gradient is taken by extra threads.
+__global__ void conv_wgrad_kernel(const bf16 *__restrict__ x, const float *__restrict__ g, float *__restrict__ dw,
+                                  float *__restrict__ db, int B, int H, int W, int cin, int cout, int rows)
+{
+    extern __shared__ __align__(16) unsigned char smw[];
+    float *gs = reinterpret_cast<float *>(smw);                           // [W][cout]
+    bf16 *xs = reinterpret_cast<bf16 *>(gs + (size_t)W * cout);           // [3][W + 2][cin]
+    const int OB = cout < 4 ? cout : 4, IB = cin < 4 ? cin : 4;
+    const int nob = cout / OB, nib = cin / IB;
+    const int nblk = 9 * nob * nib;
+    const int j = threadIdx.x;
+    int tap = 0, ob = 0, ib = 0;
+    if (j < nblk) { tap = j / (nob * nib); ob = (j / nib) % nob; ib = j % nib; }
+    const int dxo = tap % 3 - 1, dyr = tap / 3;   // staged row dyr = input row h + tap/3 - 1
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+    float bacc = 0.f;
+    const int r0 = blockIdx.x * rows, r1 = min(r0 + rows, B * H);
+    for (int r = r0; r < r1; ++r) {
+        const int bb = r / H, hh = r - bb * H;
+        __syncthreads();
+        for (int k = threadIdx.x; k < W * cout; k += blockDim.x) gs[k] = g[(size_t)r * W * cout + k];
+        for (int k = threadIdx.x; k < 3 * (W + 2) * cin; k += blockDim.x) {
+            const int rr = k / ((W + 2) * cin), rem = k - rr * (W + 2) * cin;
+            const int p = rem / cin, i = rem - p * cin;
+            const int y0 = hh + rr - 1, x0 = p - 1;
+            xs[k] = (y0 >= 0 && y0 < H && x0 >= 0 && x0 < W) ? x[(((size_t)bb * H + y0) * W + x0) * cin + i]
+                                                          : __float2bfloat16(0.f);
+        }
+        __syncthreads();
+        if (j < nblk) {
+            const bf16 *xr = xs + ((size_t)dyr * (W + 2) + 1 + dxo) * cin + ib * IB;
+            const float *gr = gs + ob * OB;
+            for (int w = 0; w < W; ++w) {
+                float gv[4], xv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) gv[a] = a < OB ? gr[(size_t)w * cout + a] : 0.f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) xv[c] = c < IB ? __bfloat162float(xr[(size_t)w * cin + c]) : 0.f;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][c] = __fmaf_rn(gv[a], xv[c], acc[a][c]);
+            }
+        } else if (j < nblk + cout) {
+            const int o = j - nblk;
+            for (int w = 0; w < W; ++w) bacc += gs[(size_t)w * cout + o];
+        }
+    }
+    if (j < nblk) {
+        for (int a = 0; a < OB; ++a)
+            for (int c = 0; c < IB; ++c)
+                atomicAdd(dw + ((size_t)(ob * OB + a) * 9 + tap) * cin + ib * IB + c, acc[a][c]);
+    } else if (j < nblk + cout) {
+        atomicAdd(db + (j - nblk), bacc);
+    }
+}
+
+// W'[i, 2-ky, 2-kx, o] = W[o, ky, kx, i] (the input gradient as a forward convolution)
+__global__ void flip_weights_kernel(const bf16 *__restrict__ w, bf16 *__restrict__ wf, int cin, int cout)
+{
+    const int n = cout * 9 * cin;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int o = j / (9 * cin), rem = j - o * 9 * cin, tap = rem / cin, i = rem - tap * cin;
+        wf[((size_t)i * 9 + (8 - tap)) * cout + o] = w[j];
+    }
+}
+
+}  // namespace
+}  // namespace spx
+
+extern "C" {
+
+sp_status sp_conv3x3_fwd(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, const void *x, const void *w,
+                         const float *bias, int32_t relu, void *y, void *stream)
+{
+    spx::clear_error();
+    if (B < 1 || H < 1 || W < 1) return spx::record_error(SP_EINVAL, "B, H, W must be >= 1");
+    const bool inner = cin == 32 && cout == 32, edge = (cin == 1 && cout == 32) || (cin == 32 && cout == 1);
+    if (!inner && !edge) return spx::record_error(SP_EINVAL, "supported channels: 1->32, 32->32, 32->1");
+    if (!x || !w || !y) return spx::record_error(SP_EINVAL, "NULL pointer");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(y)) & 15)
+        return spx::record_error(SP_EINVAL, "x, w, y must be 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const spx::bf16 *xb = static_cast<const spx::bf16 *>(x), *wb = static_cast<const spx::bf16 *>(w);
+    if (inner) {
+        const int tiles = (W + spx::kTileW - 1) / spx::kTileW;
+        const int64_t grid = (int64_t)B * H * tiles;
+        if (grid > 0x7fffffff) return spx::record_error(SP_EINVAL, "too many tiles");
+        spx::conv32_fwd_kernel<<<(unsigned)grid, 128, 0, s>>>(xb, wb, bias, static_cast<spx::bf16 *>(y), B, H, W,
+                                                             relu);
+    } else {
+        const int64_t n = (int64_t)B * H * W;
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        spx::conv_edge_fwd_kernel<<<(unsigned)blocks, 256, 0, s>>>(xb, wb, bias, y, B, H, W, cin, cout, relu);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SP_OK : spx::record_error(SP_ECUDA, cudaGetErrorString(e));
+}
+
+sp_status sp_conv3x3_bwd_data(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, const float *g,
+                              const void *w, const void *gate, float *dx, void *stream)
+{
+    spx::clear_error();
+    if (B < 1 || H < 1 || W < 1) return spx::record_error(SP_EINVAL, "B, H, W must be >= 1");
+    if (!((cin == 32 && (cout == 32 || cout == 1)) || (cin == 1 && cout == 32)))
+        return spx::record_error(SP_EINVAL, "supported channels: 1->32, 32->32, 32->1");
+    if (!g || !w || !dx) return spx::record_error(SP_EINVAL, "NULL pointer");
+    const int64_t n = (int64_t)B * H * W;
+    int64_t blocks = (n + 127) / 128;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const spx::bf16 *wb = static_cast<const spx::bf16 *>(w), *gb = static_cast<const spx::bf16 *>(gate);
+    if (cin == 32 && cout == 32)
+        spx::conv_dgrad_kernel<32, 32><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W);
+    else if (cin == 32)
+        spx::conv_dgrad_kernel<32, 1><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W);
+    else
+        spx::conv_dgrad_kernel<1, 32><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SP_OK : spx::record_error(SP_ECUDA, cudaGetErrorString(e));
+}
+
+sp_status sp_conv3x3_bwd_weight(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, const void *x,
+                                const float *g, float *dw, float *dbias, void *stream)
+{
+    spx::clear_error();
+    if (B < 1 || H < 1 || W < 1) return spx::record_error(SP_EINVAL, "B, H, W must be >= 1");
+    if (!((cin == 32 && (cout == 32 || cout == 1)) || (cin == 1 && cout == 32)))
+        return spx::record_error(SP_EINVAL, "supported channels: 1->32, 32->32, 32->1");
+    if (!x || !g || !dw || !dbias) return spx::record_error(SP_EINVAL, "NULL pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * (size_t)cout * 9 * cin, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dbias, 0, sizeof(float) * (size_t)cout, s);
+    const size_t sh = sizeof(float) * (size_t)W * cout + sizeof(spx::bf16) * 3 * (size_t)(W + 2) * cin;
+    if (sh > 200 * 1024) return spx::record_error(SP_EINVAL, "image too wide for the weight-gradient kernel");
+    const int OB = cout < 4 ? cout : 4, IB = cin < 4 ? cin : 4;
+    int threads = 9 * (cout / OB) * (cin / IB) + cout;
+    threads = (threads + 31) / 32 * 32;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spx::conv_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e == cudaSuccess) {
+        const int rows = 16;
+        const int blocks = (B * H + rows - 1) / rows;
+        spx::conv_wgrad_kernel<<<blocks, threads, sh, s>>>(static_cast<const spx::bf16 *>(x), g, dw, dbias, B, H, W,
+                                                           cin, cout, rows);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? SP_OK : spx::record_error(SP_ECUDA, cudaGetErrorString(e));
+}
+
+sp_status sp_conv3x3_flip_weights(int32_t cin, int32_t cout, const void *w, void *wf, void *stream)
+{
+    spx::clear_error();
+    if (cin < 1 || cout < 1 || !w || !wf) return spx::record_error(SP_EINVAL, "bad arguments");
+    const int n = cout * 9 * cin;
+    spx::flip_weights_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const spx::bf16 *>(w), static_cast<spx::bf16 *>(wf), cin, cout);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SP_OK : spx::record_error(SP_ECUDA, cudaGetErrorString(e));
+}
+
+}  // extern "C"

@@ -24,6 +24,7 @@ import numpy as np
 __all__ = [
     "ellipse_phantom", "Geometry", "Workload", "workload", "crop_workload",
     "random_lines_circle", "poisson_counts", "transmission_data", "batch_instance",
+    "warmstart_params", "ellipse_images_torch",
 ]
 
 
@@ -217,3 +218,46 @@ def batch_instance(i: int, scale: float = 1.0) -> Workload:
             geo = Geometry("fan", view_angle=_angles(n_view, 2.0 * math.pi), n_det=n_det,
                            det0=-0.5 * (n_det - 1), ddet=1.0, dso=1000.0 * n / 512.0, dod=500.0 * n / 512.0)
     return Workload(f"batch{i}", n, degree, 1.0, geo, coef, 1000 + i)
+
+
+def warmstart_params(seed: int, n: int = 256):
+    """Phantom and dose of one sample of the warm-start data set.
+
+    numpy default_rng(seed): number of ellipses U{5..40}, then per ellipse
+    the recipe of :func:`ellipse_phantom` (centre, semi-axes, rotation,
+    intensity) at the scale n/64, then the dose I0 log-uniform in
+    [1e3, 1e5].  Returns (params float64 [k][6] = x0, y0, ax, ay, rot,
+    intensity; I0).  Training seeds are 1e6 + i, held-out seeds 2e6 + i."""
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(5, 41))
+    s = n / 64.0
+    radius, lo, hi = 24.0 * s, 2.0 * s, 16.0 * s
+    out = np.empty((k, 6))
+    for e in range(k):
+        r = radius * math.sqrt(rng.uniform())
+        a = 2.0 * math.pi * rng.uniform()
+        out[e, 0], out[e, 1] = r * math.cos(a), r * math.sin(a)
+        out[e, 2] = rng.uniform(lo, hi)
+        out[e, 3] = rng.uniform(lo, hi)
+        out[e, 4] = rng.uniform(0.0, math.pi)
+        out[e, 5] = rng.uniform(-0.5, 1.0)
+    I0 = float(math.exp(rng.uniform(math.log(1e3), math.log(1e5))))
+    return out, I0
+
+
+def ellipse_images_torch(params_list, n: int, device, h: float = 1.0):
+    """Rasterise ellipse parameter sets (see :func:`warmstart_params`) at the
+    nodes of an n x n grid, as :func:`ellipse_phantom` does, on `device`:
+    float32 [len(params_list)][n][n]."""
+    import torch
+    c = (torch.arange(n, device=device, dtype=torch.float64) - 0.5 * (n - 1)) * h
+    Y, X = torch.meshgrid(c, c, indexing="ij")
+    out = torch.zeros((len(params_list), n, n), device=device, dtype=torch.float64)
+    for b, prm in enumerate(params_list):
+        P = torch.as_tensor(prm, device=device, dtype=torch.float64)
+        x0, y0, ax, ay, rot, inten = (P[:, k, None, None] for k in range(6))
+        dx, dy = X - x0, Y - y0
+        u = (dx * torch.cos(rot) + dy * torch.sin(rot)) / ax
+        v = (-dx * torch.sin(rot) + dy * torch.cos(rot)) / ay
+        out[b] = (inten * (u * u + v * v <= 1.0)).sum(dim=0)
+    return out.float()
