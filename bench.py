@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true", help="skip the CGLS timing (not part of the step)")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch timing (not part of the step)")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start timing (not part of the step)")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="size scale of the uneven batch")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="fan512_cubic (the benchmark) or fan256_cubic (small profiling case)")
@@ -230,6 +231,30 @@ def run_batch(args, sp, dev, stream, count=64):
     return out
 
 
+def run_warmstart(sp, dev, n_test=16, tol=1e-4):
+    """Learned-vs-cold CGLS to a relative normal-equation residual of 1e-4 on
+    held-out samples (256^2 cubic, parallel 360 x 384, Poisson data), with the
+    committed network; times include the network's forward."""
+    from paper_2503_20907_gb300 import warmstart as wsm
+    net, meta = wsm.load_net(wsm.DEFAULT_WEIGHTS, dev)
+    res, _ = wsm.evaluate(net, meta, n_test=n_test, tol=tol, log=lambda *_: None)
+    import torch
+    zz = torch.zeros(1, 256, 256, device=dev)
+    with torch.no_grad():
+        for _ in range(3):
+            net(zz)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            net(zz)
+        b.record()
+        b.synchronize()
+    res["network_ms"] = a.elapsed_time(b) / 10
+    res["workload"] = ("256x256 cubic, parallel 360 x 384, held-out phantoms (seeds 2e6+i), Poisson data at "
+                       "log-uniform dose; committed weights")
+    return res
+
+
 def run_ours(args, rank, ws, local):
     import numpy as np
     import torch
@@ -341,6 +366,7 @@ def run_ours(args, rank, ws, local):
               "kernels_per_iter": 8}
 
     batch = None if args.no_batch else run_batch(args, sp, dev, stream)
+    warm = None if args.no_warm else run_warmstart(sp, dev)
 
     if rank != 0:
         return
@@ -379,6 +405,8 @@ def run_ours(args, rank, ws, local):
         line["cg"] = cg
     if batch is not None:
         line["batch"] = batch
+    if warm is not None:
+        line["warm_start"] = warm
     if ws == 1 and not args.no_cpu_baseline and wl.name == WORKLOAD:
         cb = oracle_sample(wl)
         cb.pop("seconds", None)

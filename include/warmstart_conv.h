@@ -5,10 +5,10 @@
  * No counterpart in the paper: the network maps the backprojection A^T y to
  * an initial guess of the coefficients (it does not change the projector).
  *
- * All layers: 3x3 cross-correlation, stride 1, zero padding 1, NHWC tensors
- * [B][H][W][C] with B, H, W >= 1, channels (cin, cout) in {(1, 32),
- * (32, 32), (32, 1)}:
- *   y[b,h,w,o] = bias[o] + sum_{ky,kx,i} x[b,h+ky-1,w+kx-1,i] W[o,ky,kx,i].
+ * All layers: 3x3 cross-correlation with taps d = dilation (1..16) apart,
+ * stride 1, zero padding d, NHWC tensors [B][H][W][C] with B, H, W >= 1,
+ * channels (cin, cout) in {(1, 32), (32, 32), (32, 1)}:
+ *   y[b,h,w,o] = bias[o] + sum_{ky,kx,i} x[b,h+(ky-1)d,w+(kx-1)d,i] W[o,ky,kx,i].
  * Weights W are BF16 [cout][3][3][cin]; bias FP32 [cout] (NULL = 0).
  * Activations x are BF16; products accumulate in FP32.  All pointers are
  * device pointers, 16-byte aligned; work is enqueued on `stream`.  Host
@@ -28,22 +28,22 @@ extern "C" {
  * (mma.sync, BF16 inputs, FP32 accumulation); 1 -> 32 and 32 -> 1 on the
  * CUDA cores. */
 sp_status sp_conv3x3_fwd(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,
-                         const void *x, const void *w, const float *bias, int32_t relu,
+                         int32_t dilation, const void *x, const void *w, const float *bias, int32_t relu,
                          void *y, void *stream);
 
-/* Input gradient: dx[b,h,w,i] = sum_{ky,kx,o} g[b,h-ky+1,w-kx+1,o] W[o,ky,kx,i]
+/* Input gradient: dx[b,h,w,i] = sum_{ky,kx,o} g[b,h-(ky-1)d,w-(kx-1)d,o] W[o,ky,kx,i]
  * with g FP32 [B][H][W][cout] and dx FP32 [B][H][W][cin]; if gate != NULL
  * (BF16 [B][H][W][cin]) dx is zeroed where gate <= 0 (ReLU of the layer
  * below). */
 sp_status sp_conv3x3_bwd_data(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,
-                              const float *g, const void *w, const void *gate, float *dx,
+                              int32_t dilation, const float *g, const void *w, const void *gate, float *dx,
                               void *stream);
 
-/* Weight gradient: dw[o,ky,kx,i] = sum_{b,h,w} g[b,h,w,o] x[b,h+ky-1,w+kx-1,i]
+/* Weight gradient: dw[o,ky,kx,i] = sum_{b,h,w} g[b,h,w,o] x[b,h+(ky-1)d,w+(kx-1)d,i]
  * (FP32 [cout][3][3][cin], overwritten) and dbias[o] = sum g[b,h,w,o]
  * (FP32 [cout], overwritten).  x BF16 [B][H][W][cin], g FP32. */
 sp_status sp_conv3x3_bwd_weight(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,
-                                const void *x, const float *g, float *dw, float *dbias,
+                                int32_t dilation, const void *x, const float *g, float *dw, float *dbias,
                                 void *stream);
 
 /* wf[i][2-ky][2-kx][o] = w[o][ky][kx][i] (BF16): the input gradient written

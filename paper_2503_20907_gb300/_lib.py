@@ -108,11 +108,11 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
     lib.spline_batch_destroy.argtypes = [P]
     i32 = ctypes.c_int32
     lib.sp_conv3x3_fwd.restype = st
-    lib.sp_conv3x3_fwd.argtypes = [i32, i32, i32, i32, i32, P, P, P, i32, P, P]
+    lib.sp_conv3x3_fwd.argtypes = [i32, i32, i32, i32, i32, i32, P, P, P, i32, P, P]
     lib.sp_conv3x3_bwd_data.restype = st
-    lib.sp_conv3x3_bwd_data.argtypes = [i32, i32, i32, i32, i32, P, P, P, P, P]
+    lib.sp_conv3x3_bwd_data.argtypes = [i32, i32, i32, i32, i32, i32, P, P, P, P, P]
     lib.sp_conv3x3_bwd_weight.restype = st
-    lib.sp_conv3x3_bwd_weight.argtypes = [i32, i32, i32, i32, i32, P, P, P, P, P]
+    lib.sp_conv3x3_bwd_weight.argtypes = [i32, i32, i32, i32, i32, i32, P, P, P, P, P]
     lib.sp_conv3x3_flip_weights.restype = st
     lib.sp_conv3x3_flip_weights.argtypes = [i32, i32, P, P, P]
     lib.spline_plan_destroy.restype = st

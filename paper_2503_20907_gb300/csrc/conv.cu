@@ -2,6 +2,8 @@
 // stride 1, zero padding 1, NHWC, BF16 activations and weights, FP32
 // accumulation.
 //
+// Taps may be dilated (offsets -d, 0, d).
+//
 //   forward, 32 -> 32 channels: implicit GEMM on the tensor cores
 //     (mma.sync m16n8k16, BF16 in, FP32 accumulate).  A CTA takes 64 pixels
 //     of one image row; the three input rows it needs and the weights are
@@ -28,6 +30,7 @@ constexpr int kC = 32;              // channels of the inner layers
 constexpr int kTileW = 64;          // pixels of one CTA (4 warps x 16)
 constexpr int kXStride = 40;        // bf16 per staged pixel (32 + 8: conflict-free fragment loads)
 constexpr int kWStride = 9 * kC + 8;   // bf16 per staged output channel
+constexpr int kMaxDil = 16;         // largest dilation of the taps
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1)
@@ -39,12 +42,12 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// y = conv(x) + bias (ReLU optional), 32 -> 32 channels.
+// y = conv(x) + bias (ReLU optional), 32 -> 32 channels, taps dil apart.
 __global__ void __launch_bounds__(128) conv32_fwd_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
                                                          const float *__restrict__ bias, bf16 *__restrict__ y,
-                                                         int B, int H, int W, int relu)
+                                                         int B, int H, int W, int relu, int dil)
 {
-    __shared__ __align__(16) bf16 xs[3][kTileW + 2][kXStride];
+    __shared__ __align__(16) bf16 xs[3][kTileW + 2 * kMaxDil][kXStride];
     __shared__ __align__(16) bf16 ws[kC][kWStride];
     const int tiles_w = (W + kTileW - 1) / kTileW;
     const int tw = blockIdx.x % tiles_w;
@@ -56,11 +59,12 @@ __global__ void __launch_bounds__(128) conv32_fwd_kernel(const bf16 *__restrict_
         const int o = i / 36, c = i - o * 36;
         *reinterpret_cast<uint4 *>(&ws[o][c * 8]) = *reinterpret_cast<const uint4 *>(w + (size_t)o * 9 * kC + c * 8);
     }
-    // input rows h-1..h+1, pixels w0-1..w0+64, 16-byte chunks of 8 channels
-    for (int i = threadIdx.x; i < 3 * (kTileW + 2) * 4; i += 128) {
-        const int r = i / ((kTileW + 2) * 4), rem = i - r * (kTileW + 2) * 4;
+    // input rows h-dil, h, h+dil, pixels w0-dil..w0+63+dil, 16-byte chunks of 8 channels
+    const int tw2 = kTileW + 2 * dil;
+    for (int i = threadIdx.x; i < 3 * tw2 * 4; i += 128) {
+        const int r = i / (tw2 * 4), rem = i - r * tw2 * 4;
         const int p = rem >> 2, c = rem & 3;
-        const int hh = h + r - 1, ww = w0 + p - 1;
+        const int hh = h + (r - 1) * dil, ww = w0 + p - dil;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (hh >= 0 && hh < H && ww >= 0 && ww < W)
             v = *reinterpret_cast<const uint4 *>(x + (((size_t)b * H + hh) * W + ww) * kC + c * 8);
@@ -81,10 +85,11 @@ __global__ void __launch_bounds__(128) conv32_fwd_kernel(const bf16 *__restrict_
 #pragma unroll
         for (int cb = 0; cb < 2; ++cb) {
             const int c0 = cb * 16 + 2 * t;
-            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(&xs[ky][pb + g + kx][c0]);
-            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(&xs[ky][pb + g + 8 + kx][c0]);
-            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(&xs[ky][pb + g + kx][c0 + 8]);
-            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(&xs[ky][pb + g + 8 + kx][c0 + 8]);
+            const int px = pb + g + kx * dil;
+            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(&xs[ky][px][c0]);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(&xs[ky][px + 8][c0]);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(&xs[ky][px][c0 + 8]);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(&xs[ky][px + 8][c0 + 8]);
             const int k0 = tap * kC + cb * 16 + 2 * t;
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
@@ -116,7 +121,7 @@ __device__ __forceinline__ float ld_act(const bf16 *p) { return __bfloat162float
 // Forward on CUDA cores for cin = 1 (y bf16 [.., 32]) or cout = 1 (y float [..]).
 __global__ void conv_edge_fwd_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
                                      const float *__restrict__ bias, void *y, int B, int H, int W, int cin,
-                                     int cout, int relu)
+                                     int cout, int relu, int dil)
 {
     __shared__ float wsh[9 * kC];
     for (int i = threadIdx.x; i < 9 * kC; i += blockDim.x) wsh[i] = __bfloat162float(w[i]);
@@ -130,7 +135,7 @@ __global__ void conv_edge_fwd_kernel(const bf16 *__restrict__ x, const bf16 *__r
 #pragma unroll
             for (int o = 0; o < kC; ++o) acc[o] = bias ? bias[o] : 0.f;
             for (int tap = 0; tap < 9; ++tap) {
-                const int y0 = hh + tap / 3 - 1, x0 = ww + tap % 3 - 1;
+                const int y0 = hh + (tap / 3 - 1) * dil, x0 = ww + (tap % 3 - 1) * dil;
                 if (y0 < 0 || y0 >= H || x0 < 0 || x0 >= W) continue;
                 const float v = ld_act(x + (bb * H + y0) * W + x0);
 #pragma unroll
@@ -146,7 +151,7 @@ __global__ void conv_edge_fwd_kernel(const bf16 *__restrict__ x, const bf16 *__r
         } else {
             float acc = bias ? bias[0] : 0.f;
             for (int tap = 0; tap < 9; ++tap) {
-                const int y0 = hh + tap / 3 - 1, x0 = ww + tap % 3 - 1;
+                const int y0 = hh + (tap / 3 - 1) * dil, x0 = ww + (tap % 3 - 1) * dil;
                 if (y0 < 0 || y0 >= H || x0 < 0 || x0 >= W) continue;
                 const bf16 *xp = x + ((bb * H + y0) * W + x0) * kC;
 #pragma unroll
@@ -161,7 +166,7 @@ __global__ void conv_edge_fwd_kernel(const bf16 *__restrict__ x, const bf16 *__r
 // dx[p, i] = sum_{tap, o} g[p - off(tap), o] W[o, tap, i], gated by x_gate[p, i] > 0.
 template <int CIN, int COUT>
 __global__ void conv_dgrad_kernel(const float *__restrict__ g, const bf16 *__restrict__ w,
-                                  const bf16 *__restrict__ gate, float *__restrict__ dx, int B, int H, int W)
+                                  const bf16 *__restrict__ gate, float *__restrict__ dx, int B, int H, int W, int dil)
 {
     __shared__ float wsh[COUT * 9 * CIN];
     for (int i = threadIdx.x; i < COUT * 9 * CIN; i += blockDim.x) wsh[i] = __bfloat162float(w[i]);
@@ -174,7 +179,7 @@ __global__ void conv_dgrad_kernel(const float *__restrict__ g, const bf16 *__res
 #pragma unroll
         for (int i = 0; i < CIN; ++i) acc[i] = 0.f;
         for (int tap = 0; tap < 9; ++tap) {
-            const int y0 = hh - (tap / 3 - 1), x0 = ww - (tap % 3 - 1);
+            const int y0 = hh - (tap / 3 - 1) * dil, x0 = ww - (tap % 3 - 1) * dil;
             if (y0 < 0 || y0 >= H || x0 < 0 || x0 >= W) continue;
             const float *gp = g + ((bb * H + y0) * W + x0) * COUT;
 #pragma unroll 4
@@ -200,11 +205,12 @@ __global__ void conv_dgrad_kernel(const float *__restrict__ g, const bf16 *__res
 // Each thread owns a block of OB x IB outputs of one tap (OB = min(cout, 4),
 // IB = min(cin, 4)); the bias gradient is taken by extra threads.
 __global__ void conv_wgrad_kernel(const bf16 *__restrict__ x, const float *__restrict__ g, float *__restrict__ dw,
-                                  float *__restrict__ db, int B, int H, int W, int cin, int cout, int rows)
+                                  float *__restrict__ db, int B, int H, int W, int cin, int cout, int rows, int dil)
 {
     extern __shared__ __align__(16) unsigned char smw[];
     float *gs = reinterpret_cast<float *>(smw);                           // [W][cout]
-    bf16 *xs = reinterpret_cast<bf16 *>(gs + (size_t)W * cout);           // [3][W + 2][cin]
+    bf16 *xs = reinterpret_cast<bf16 *>(gs + (size_t)W * cout);           // [3][W + 2 dil][cin]
+    const int WP = W + 2 * dil;
     const int OB = cout < 4 ? cout : 4, IB = cin < 4 ? cin : 4;
     const int nob = cout / OB, nib = cin / IB;
     const int nblk = 9 * nob * nib;
@@ -223,16 +229,16 @@ __global__ void conv_wgrad_kernel(const bf16 *__restrict__ x, const float *__res
         const int bb = r / H, hh = r - bb * H;
         __syncthreads();
         for (int k = threadIdx.x; k < W * cout; k += blockDim.x) gs[k] = g[(size_t)r * W * cout + k];
-        for (int k = threadIdx.x; k < 3 * (W + 2) * cin; k += blockDim.x) {
-            const int rr = k / ((W + 2) * cin), rem = k - rr * (W + 2) * cin;
+        for (int k = threadIdx.x; k < 3 * WP * cin; k += blockDim.x) {
+            const int rr = k / (WP * cin), rem = k - rr * WP * cin;
             const int p = rem / cin, i = rem - p * cin;
-            const int y0 = hh + rr - 1, x0 = p - 1;
+            const int y0 = hh + (rr - 1) * dil, x0 = p - dil;
             xs[k] = (y0 >= 0 && y0 < H && x0 >= 0 && x0 < W) ? x[(((size_t)bb * H + y0) * W + x0) * cin + i]
                                                           : __float2bfloat16(0.f);
         }
         __syncthreads();
         if (j < nblk) {
-            const bf16 *xr = xs + ((size_t)dyr * (W + 2) + 1 + dxo) * cin + ib * IB;
+            const bf16 *xr = xs + ((size_t)dyr * WP + dil + dxo * dil) * cin + ib * IB;
             const float *gr = gs + ob * OB;
             for (int w = 0; w < W; ++w) {
                 float gv[4], xv[4];
@@ -274,11 +280,12 @@ __global__ void flip_weights_kernel(const bf16 *__restrict__ w, bf16 *__restrict
 
 extern "C" {
 
-sp_status sp_conv3x3_fwd(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, const void *x, const void *w,
-                         const float *bias, int32_t relu, void *y, void *stream)
+sp_status sp_conv3x3_fwd(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dilation,
+                         const void *x, const void *w, const float *bias, int32_t relu, void *y, void *stream)
 {
     spx::clear_error();
     if (B < 1 || H < 1 || W < 1) return spx::record_error(SP_EINVAL, "B, H, W must be >= 1");
+    if (dilation < 1 || dilation > spx::kMaxDil) return spx::record_error(SP_EINVAL, "dilation must be 1..16");
     const bool inner = cin == 32 && cout == 32, edge = (cin == 1 && cout == 32) || (cin == 32 && cout == 1);
     if (!inner && !edge) return spx::record_error(SP_EINVAL, "supported channels: 1->32, 32->32, 32->1");
     if (!x || !w || !y) return spx::record_error(SP_EINVAL, "NULL pointer");
@@ -291,22 +298,24 @@ sp_status sp_conv3x3_fwd(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t c
         const int64_t grid = (int64_t)B * H * tiles;
         if (grid > 0x7fffffff) return spx::record_error(SP_EINVAL, "too many tiles");
         spx::conv32_fwd_kernel<<<(unsigned)grid, 128, 0, s>>>(xb, wb, bias, static_cast<spx::bf16 *>(y), B, H, W,
-                                                             relu);
+                                                             relu, dilation);
     } else {
         const int64_t n = (int64_t)B * H * W;
         int64_t blocks = (n + 255) / 256;
         if (blocks > 152 * 16) blocks = 152 * 16;
-        spx::conv_edge_fwd_kernel<<<(unsigned)blocks, 256, 0, s>>>(xb, wb, bias, y, B, H, W, cin, cout, relu);
+        spx::conv_edge_fwd_kernel<<<(unsigned)blocks, 256, 0, s>>>(xb, wb, bias, y, B, H, W, cin, cout, relu,
+                                                                   dilation);
     }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SP_OK : spx::record_error(SP_ECUDA, cudaGetErrorString(e));
 }
 
-sp_status sp_conv3x3_bwd_data(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, const float *g,
-                              const void *w, const void *gate, float *dx, void *stream)
+sp_status sp_conv3x3_bwd_data(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dilation,
+                              const float *g, const void *w, const void *gate, float *dx, void *stream)
 {
     spx::clear_error();
     if (B < 1 || H < 1 || W < 1) return spx::record_error(SP_EINVAL, "B, H, W must be >= 1");
+    if (dilation < 1 || dilation > spx::kMaxDil) return spx::record_error(SP_EINVAL, "dilation must be 1..16");
     if (!((cin == 32 && (cout == 32 || cout == 1)) || (cin == 1 && cout == 32)))
         return spx::record_error(SP_EINVAL, "supported channels: 1->32, 32->32, 32->1");
     if (!g || !w || !dx) return spx::record_error(SP_EINVAL, "NULL pointer");
@@ -316,27 +325,28 @@ sp_status sp_conv3x3_bwd_data(int32_t B, int32_t H, int32_t W, int32_t cin, int3
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const spx::bf16 *wb = static_cast<const spx::bf16 *>(w), *gb = static_cast<const spx::bf16 *>(gate);
     if (cin == 32 && cout == 32)
-        spx::conv_dgrad_kernel<32, 32><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W);
+        spx::conv_dgrad_kernel<32, 32><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W, dilation);
     else if (cin == 32)
-        spx::conv_dgrad_kernel<32, 1><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W);
+        spx::conv_dgrad_kernel<32, 1><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W, dilation);
     else
-        spx::conv_dgrad_kernel<1, 32><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W);
+        spx::conv_dgrad_kernel<1, 32><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W, dilation);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SP_OK : spx::record_error(SP_ECUDA, cudaGetErrorString(e));
 }
 
-sp_status sp_conv3x3_bwd_weight(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, const void *x,
-                                const float *g, float *dw, float *dbias, void *stream)
+sp_status sp_conv3x3_bwd_weight(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dilation,
+                                const void *x, const float *g, float *dw, float *dbias, void *stream)
 {
     spx::clear_error();
     if (B < 1 || H < 1 || W < 1) return spx::record_error(SP_EINVAL, "B, H, W must be >= 1");
+    if (dilation < 1 || dilation > spx::kMaxDil) return spx::record_error(SP_EINVAL, "dilation must be 1..16");
     if (!((cin == 32 && (cout == 32 || cout == 1)) || (cin == 1 && cout == 32)))
         return spx::record_error(SP_EINVAL, "supported channels: 1->32, 32->32, 32->1");
     if (!x || !g || !dw || !dbias) return spx::record_error(SP_EINVAL, "NULL pointer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * (size_t)cout * 9 * cin, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dbias, 0, sizeof(float) * (size_t)cout, s);
-    const size_t sh = sizeof(float) * (size_t)W * cout + sizeof(spx::bf16) * 3 * (size_t)(W + 2) * cin;
+    const size_t sh = sizeof(float) * (size_t)W * cout + sizeof(spx::bf16) * 3 * (size_t)(W + 2 * dilation) * cin;
     if (sh > 200 * 1024) return spx::record_error(SP_EINVAL, "image too wide for the weight-gradient kernel");
     const int OB = cout < 4 ? cout : 4, IB = cin < 4 ? cin : 4;
     int threads = 9 * (cout / OB) * (cin / IB) + cout;
@@ -346,7 +356,7 @@ sp_status sp_conv3x3_bwd_weight(int32_t B, int32_t H, int32_t W, int32_t cin, in
         const int rows = 16;
         const int blocks = (B * H + rows - 1) / rows;
         spx::conv_wgrad_kernel<<<blocks, threads, sh, s>>>(static_cast<const spx::bf16 *>(x), g, dw, dbias, B, H, W,
-                                                           cin, cout, rows);
+                                                           cin, cout, rows, dilation);
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? SP_OK : spx::record_error(SP_ECUDA, cudaGetErrorString(e));

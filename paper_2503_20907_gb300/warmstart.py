@@ -4,7 +4,7 @@ A small CNN maps the scaled backprojection z = alpha A^T b of noisy data b to
 an initial guess x_0 = z + f(z) of the spline coefficients; CGLS
 (Plan.cgls) then starts from x_0 instead of 0, and plain CGLS from 0 stays
 the fallback.  f has six 3x3 convolution layers (1 -> 32, four 32 -> 32,
-32 -> 1) with ReLU between them, BF16 weights and activations and FP32
+32 -> 1; taps 1, 2, 4, 8, 16, 1 apart) with ReLU between them, BF16 weights and activations and FP32
 accumulation, all in this library's kernels (include/warmstart_conv.h):
 the forward of the inner layers on the tensor cores, the gradients on the
 CUDA cores.  Training data (phantom, sinogram, backprojection) come from the
@@ -26,31 +26,37 @@ import torch
 from . import _lib
 from ._lib import Grid, Lines, Plan, _check, _stream, load
 
+from pathlib import Path
+
 CH = 32
-LAYERS = ((1, CH, True), (CH, CH, True), (CH, CH, True), (CH, CH, True), (CH, CH, True), (CH, 1, False))
+DEFAULT_WEIGHTS = Path(__file__).resolve().parent / "weights" / "warmstart_parallel256.pt"
+# (cin, cout, relu, dilation): 3x3 taps spread 1, 2, 4, 8, 16, 1 apart, a
+# receptive field of 65 x 65 nodes (the normal operator A^T A is non-local)
+LAYERS = ((1, CH, True, 1), (CH, CH, True, 2), (CH, CH, True, 4), (CH, CH, True, 8), (CH, CH, True, 16),
+          (CH, 1, False, 1))
 
 
 class _Conv3x3(torch.autograd.Function):
     """One layer: y = relu?(conv3x3(x) + bias) with this library's kernels."""
 
     @staticmethod
-    def forward(ctx, x, w, b, cin, cout, relu):
+    def forward(ctx, x, w, b, cin, cout, relu, dil):
         B, H, W = x.shape[0], x.shape[1], x.shape[2]
         wb = w.detach().to(torch.bfloat16).contiguous()
         if cout == 1:
             y = torch.empty((B, H, W), dtype=torch.float32, device=x.device)
         else:
             y = torch.empty((B, H, W, cout), dtype=torch.bfloat16, device=x.device)
-        _check(load().sp_conv3x3_fwd(B, H, W, cin, cout, x.data_ptr(), wb.data_ptr(), b.detach().data_ptr(),
+        _check(load().sp_conv3x3_fwd(B, H, W, cin, cout, dil, x.data_ptr(), wb.data_ptr(), b.detach().data_ptr(),
                                      int(relu), y.data_ptr(), _stream(None)))
         ctx.save_for_backward(x, wb, y)
-        ctx.meta = (cin, cout, relu)
+        ctx.meta = (cin, cout, relu, dil)
         return y
 
     @staticmethod
     def backward(ctx, gy):
         x, wb, y = ctx.saved_tensors
-        cin, cout, relu = ctx.meta
+        cin, cout, relu, dil = ctx.meta
         B, H, W = x.shape[0], x.shape[1], x.shape[2]
         g = gy.float()
         if relu:
@@ -59,19 +65,19 @@ class _Conv3x3(torch.autograd.Function):
         dx = None
         if ctx.needs_input_grad[0]:
             dxf = torch.empty((B, H, W, cin), dtype=torch.float32, device=x.device)
-            _check(load().sp_conv3x3_bwd_data(B, H, W, cin, cout, g.data_ptr(), wb.data_ptr(), None,
+            _check(load().sp_conv3x3_bwd_data(B, H, W, cin, cout, dil, g.data_ptr(), wb.data_ptr(), None,
                                               dxf.data_ptr(), _stream(None)))
             dx = dxf.to(x.dtype)
         dw = torch.empty((cout, 3, 3, cin), dtype=torch.float32, device=x.device)
         db = torch.empty(cout, dtype=torch.float32, device=x.device)
-        _check(load().sp_conv3x3_bwd_weight(B, H, W, cin, cout, x.data_ptr(), g.data_ptr(), dw.data_ptr(),
+        _check(load().sp_conv3x3_bwd_weight(B, H, W, cin, cout, dil, x.data_ptr(), g.data_ptr(), dw.data_ptr(),
                                             db.data_ptr(), _stream(None)))
-        return dx, dw, db, None, None, None
+        return dx, dw, db, None, None, None, None
 
 
-def conv3x3(x, w, b, relu: bool):
+def conv3x3(x, w, b, relu: bool, dil: int = 1):
     """x BF16 [B,H,W,cin], w FP32 master weights [cout,3,3,cin] (used as BF16), b FP32 [cout]."""
-    return _Conv3x3.apply(x, w, b, int(w.shape[3]), int(w.shape[0]), bool(relu))
+    return _Conv3x3.apply(x, w, b, int(w.shape[3]), int(w.shape[0]), bool(relu), int(dil))
 
 
 class WarmStartNet(torch.nn.Module):
@@ -82,7 +88,7 @@ class WarmStartNet(torch.nn.Module):
         g = torch.Generator().manual_seed(seed)
         self.w = torch.nn.ParameterList()
         self.b = torch.nn.ParameterList()
-        for k, (cin, cout, _) in enumerate(LAYERS):
+        for k, (cin, cout, _, _) in enumerate(LAYERS):
             std = math.sqrt(2.0 / (9 * cin))
             w = torch.randn((cout, 3, 3, cin), generator=g) * std
             if k == len(LAYERS) - 1:
@@ -92,8 +98,8 @@ class WarmStartNet(torch.nn.Module):
 
     def forward(self, z):
         x = z.to(torch.bfloat16).unsqueeze(-1).contiguous()
-        for k, (_, _, relu) in enumerate(LAYERS):
-            x = conv3x3(x, self.w[k], self.b[k], relu)
+        for k, (_, _, relu, dil) in enumerate(LAYERS):
+            x = conv3x3(x, self.w[k], self.b[k], relu, dil)
         return z + x
 
 
@@ -213,6 +219,28 @@ def load_net(path, device="cuda"):
     return net.to(device), d["meta"]
 
 
+# ------------------------------------------------------------------ solving
+def solve(plan: Plan, b, net=None, alpha: float | None = None, tol: float = 1e-4, max_iters: int = 600):
+    """CGLS to ||A^T (b - A x)|| < tol ||A^T b||, warm-started by the network
+    when one is given; plain CGLS from 0 is the fallback when the warm start
+    does not reach the tolerance.  Returns (x, iterations, warm_used)."""
+    x_cold, gc = plan.cgls(b, 0)
+    g0 = float(gc[0])
+    if net is not None:
+        with torch.no_grad():
+            z = plan.adj(b) * alpha
+            x0 = net(z.unsqueeze(0))[0]
+        _, gw = plan.cgls(b, max_iters, x0=x0)
+        k = iterations_to(gw.cpu().numpy(), g0, tol)
+        if k is not None:
+            x, _ = plan.cgls(b, k, x0=x0, history=False)
+            return x, k, True
+    _, gcold = plan.cgls(b, max_iters)
+    k = iterations_to(gcold.cpu().numpy(), g0, tol)
+    x, _ = plan.cgls(b, k if k is not None else max_iters, history=False)
+    return x, k, False
+
+
 # ------------------------------------------------------------------ evaluation
 def iterations_to(gam: np.ndarray, gamma0: float, tol: float) -> int | None:
     r = np.sqrt(np.maximum(gam, 0.0) / gamma0)
@@ -227,7 +255,7 @@ def evaluate(net, meta, n_test=256, tol=1e-4, max_iters=600, device="cuda", log=
     plan = Plan(grid, lines)
     z, c, b, _ = make_samples(plan, [2_000_000 + i for i in range(n_test)], device, meta["alpha"])
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))  # noqa: E731
-    rows = []
+    rows, loose, start = [], [], []
     plan.cgls(b[0], 2)
     for k in range(n_test):
         _, gc = plan.cgls(b[k], max_iters)
@@ -236,7 +264,10 @@ def evaluate(net, meta, n_test=256, tol=1e-4, max_iters=600, device="cuda", log=
         with torch.no_grad():
             x0 = net(z[k:k + 1])[0]
         _, gw = plan.cgls(b[k], max_iters, x0=x0)
-        kc, kw = iterations_to(gc, g0, tol), iterations_to(gw.cpu().numpy(), g0, tol)
+        gwn = gw.cpu().numpy()
+        kc, kw = iterations_to(gc, g0, tol), iterations_to(gwn, g0, tol)
+        loose.append([(iterations_to(gc, g0, t), iterations_to(gwn, g0, t)) for t in (1e-2, 1e-3)])
+        start.append(float(np.sqrt(gwn[0] / g0)))
         tc = tw = None
         if kc is not None:
             a, e = ev()
@@ -256,6 +287,14 @@ def evaluate(net, meta, n_test=256, tol=1e-4, max_iters=600, device="cuda", log=
             tw = a.elapsed_time(e)
         rows.append((kc, kw, tc, tw))
     res = summarize(rows)
+    res["tol"] = tol
+    res["warm_start_rel_residual"] = {"median": float(np.median(start)), "q25": float(np.percentile(start, 25)),
+                                      "q75": float(np.percentile(start, 75))}
+    for j, t in enumerate((1e-2, 1e-3)):
+        kc = [r[j][0] for r in loose]
+        kw = [r[j][1] for r in loose]
+        res[f"iters_at_{t:g}"] = {"cold_median": float(np.median([k for k in kc if k is not None])),
+                                  "warm_median": float(np.median([k for k in kw if k is not None]))}
     log(json.dumps(res))
     return res, rows
 
@@ -280,8 +319,9 @@ def main():
     ap.add_argument("--out", default="warmstart.pt")
     ap.add_argument("--weights", default=None)
     ap.add_argument("--n-train", type=int, default=20000)
-    ap.add_argument("--epochs", type=int, default=2)
+    ap.add_argument("--epochs", type=int, default=1)
     ap.add_argument("--n-test", type=int, default=256)
+    ap.add_argument("--report", default=None, help="write the evaluation summary (JSON) here")
     a = ap.parse_args()
     if a.cmd == "train":
         net, meta = train(n_train=a.n_train, epochs=a.epochs)
@@ -289,7 +329,10 @@ def main():
         print(json.dumps(meta))
     else:
         net, meta = load_net(a.weights)
-        evaluate(net, meta, n_test=a.n_test)
+        res, _ = evaluate(net, meta, n_test=a.n_test)
+        if a.report:
+            with open(a.report, "w") as f:
+                json.dump({"meta": meta, "eval": res}, f, indent=1)
 
 
 if __name__ == "__main__":

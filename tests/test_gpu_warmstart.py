@@ -1,0 +1,70 @@
+"""The trained warm start (paper_2503_20907_gb300/weights): the network run
+through this library's kernels against the FP64 oracle layers with the same
+BF16 rounding between layers, and what it gains over plain CGLS on held-out
+samples: a smaller starting normal-equation residual, and the iteration
+count to 1e-4 (reported; the late CG iterations are dominated by components
+the network does not predict)."""
+import numpy as np
+import pytest
+
+from oracle.conv import conv3x3
+
+torch = pytest.importorskip("torch")
+sp = pytest.importorskip("paper_2503_20907_gb300")
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_2503_20907_gb300 import warmstart as ws
+    net, meta = ws.load_net(ws.DEFAULT_WEIGHTS, DEV)
+    return ws, net, meta
+
+
+def test_network_forward_matches_oracle_layers(trained):
+    ws, net, meta = trained
+    rng = np.random.default_rng(0)
+    z = torch.from_numpy(rng.standard_normal((1, 48, 80)).astype(np.float32)).to(DEV)
+    with torch.no_grad():
+        got = net(z).cpu().numpy()[0]
+    # reference: FP64 layers, activations rounded to BF16 after each layer as the kernels store them
+    x = z.to(torch.bfloat16).float().cpu().numpy()[..., None].astype(np.float64)
+    for k, (cin, cout, relu, dil) in enumerate(ws.LAYERS):
+        w = net.w[k].detach().to(torch.bfloat16).float().cpu().numpy()
+        y = conv3x3(x, w, net.b[k].detach().cpu().numpy(), d=dil)
+        if relu:
+            y = np.maximum(y, 0.0)
+        x = y if cout == 1 else torch.from_numpy(y).to(torch.bfloat16).double().numpy()
+    ref = z.cpu().numpy()[0] + x[0, :, :, 0]
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-3
+
+
+def test_warm_start_gain_on_held_out_samples(trained):
+    ws, net, meta = trained
+    grid, lines = ws.geometry(DEV)
+    plan = sp.Plan(grid, lines)
+    z, c, b, _ = ws.make_samples(plan, [2_000_000 + i for i in range(6)], DEV, meta["alpha"])
+    rel0, kc, kw = [], [], []
+    for k in range(6):
+        _, gc = plan.cgls(b[k], 800)
+        gc = gc.cpu().numpy()
+        with torch.no_grad():
+            x0 = net(z[k:k + 1])[0]
+        _, gz = plan.cgls(b[k], 0, x0=z[k])
+        _, gw = plan.cgls(b[k], 800, x0=x0)
+        gw = gw.cpu().numpy()
+        rel0.append((np.sqrt(gw[0] / gc[0]), np.sqrt(float(gz[0]) / gc[0])))
+        kc.append(ws.iterations_to(gc, gc[0], 1e-4))
+        kw.append(ws.iterations_to(gw, gc[0], 1e-4))
+    # the network's start is closer than 0 and than its input z in the normal-equation residual
+    assert all(rw < 0.5 and rw < rz for rw, rz in rel0)
+    # both reach the tolerance; the warm start is not slower by more than a few iterations
+    assert all(a is not None and b_ is not None for a, b_ in zip(kc, kw))
+    assert np.median(kw) <= np.median(kc) + 3
+    # the solver with fallback returns a solution within the tolerance either way
+    x, iters, warm = ws.solve(plan, b[0], net, meta["alpha"], tol=1e-4)
+    s = plan.adj(plan.fwd(x) - b[0])
+    s0 = plan.adj(b[0])
+    assert float(s.norm() / s0.norm()) < 5e-4   # recursive CGLS residual vs the one recomputed in FP32

@@ -45,3 +45,22 @@ def test_gradients_are_adjoints():
     dW, db = conv3x3_grad_weight(x, g)
     assert abs(lhs - float((W * dW).sum())) < 1e-10 * abs(lhs)
     assert np.allclose(db, g.sum(axis=(0, 1, 2)))
+
+
+def test_dilated_conv_is_correlation_with_spread_kernel():
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((1, 11, 13, 2))
+    W = rng.standard_normal((3, 3, 3, 2))
+    for d in (2, 3):
+        y = conv3x3(x, W, d=d)
+        for o in range(3):
+            ref = 0.0
+            for i in range(2):
+                K = np.zeros((2 * d + 1, 2 * d + 1))
+                K[::d, ::d] = W[o, :, :, i]
+                ref = ref + correlate2d(x[0, :, :, i], K, mode="same", boundary="fill")
+            assert np.allclose(y[0, :, :, o], ref, atol=1e-12)
+        g = rng.standard_normal(y.shape)
+        lhs = float((y * g).sum())
+        assert abs(lhs - float((x * conv3x3_grad_input(g, W, d=d)).sum())) < 1e-10 * abs(lhs)
+        assert abs(lhs - float((W * conv3x3_grad_weight(x, g, d=d)[0]).sum())) < 1e-10 * abs(lhs)
