@@ -35,6 +35,10 @@ UNIT = "Mrays/s"
 WORKLOAD = "fan512_cubic"
 FP32_LANES_PER_SM = 128
 KERNELS_PER_STEP = 6   # line setup, tables, transpose + forward strip, adjoint strip + transposed add
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
+# capture of these kernel versions on this workload); set to None whenever the
+# kernels change until they are captured again.
+TRAFFIC = {"fan512_cubic": {"spline_fwd": 768651776, "spline_adj": 773734144}}
 CG_ITERS = 100
 FLOPS_PER_PAIR = lambda n: 2 * (2 * n + 3)   # noqa: E731  (2n+1 Horner FMAs, 1 offset, 1 accumulate)
 
@@ -391,7 +395,8 @@ def run_ours(args, rank, ws, local):
         "slow_rows": slow_rows,
         "basis_evals_per_s": 2 * pairs * args.steps / (tot) if tot > 0 else None,
         "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": (TRAFFIC.get(wl.name) or {}).get(dom_name),
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
                                     f"x 2 x {max_mhz:.0f} MHz max SM clock",
                      "flops_per_pair": FLOPS_PER_PAIR(wl.degree)},
