@@ -228,10 +228,14 @@ sp_status spline_plan_autotune(sp_plan *plan, const float *coef, const float *si
 
 /*
  * Batches: several independent instances (each its own grid, basis, degree
- * and line list, sizes free) projected together.  A call forks the
- * instances over 8 internal streams and joins them on the caller's stream;
- * the first call for a given set of data pointers records that as a CUDA
- * graph, later calls with the same pointers replay it (one launch).
+ * and line list, sizes free) projected together.  Instances on the strip
+ * kernels (parallel and fan lists, degree >= 1, path not forced to the
+ * general kernels) share one persistent launch that takes chunks of 32
+ * lines of any of them from a work queue; the others are forked over 8
+ * internal streams; all are joined on the caller's stream.  The first call
+ * for a given set of data pointers records that as a CUDA graph (after
+ * uploading the queue, which synchronises the device), later calls with the
+ * same pointers replay it (one launch).
  *   spline_batch_create   count >= 1 instances from grids[count], lines[count]
  *                         (each as spline_plan_create; all pointers of
  *                         lines must stay valid while the batch is prepared)
@@ -255,6 +259,9 @@ sp_status spline_batch_autotune(sp_batch *batch, const float *const *coef, const
                                 void *stream, int32_t *paths);
 /* Number of instances (-1 if batch is NULL). */
 int32_t spline_batch_count(const sp_batch *batch);
+/* Number of instances that the last recorded forward (adjoint != 0: adjoint)
+ * graph runs through the work queue (-1 if batch is NULL). */
+int32_t spline_batch_queued(const sp_batch *batch, int32_t adjoint);
 sp_status spline_batch_destroy(sp_batch *batch);
 
 /* Number of lines of the plan (-1 if plan is NULL). */

@@ -47,7 +47,8 @@ EXPORTED = ("sp_lines_count", "spline_project_fwd", "spline_project_adj", "splin
             "spline_plan_adj", "spline_plan_lines", "spline_plan_destroy", "spline_plan_stats",
             "spline_project_fwd_noalloc", "spline_plan_cgls", "spline_plan_set_paths",
             "spline_plan_autotune", "spline_batch_create", "spline_batch_prepare", "spline_batch_fwd",
-            "spline_batch_adj", "spline_batch_autotune", "spline_batch_count", "spline_batch_destroy",
+            "spline_batch_adj", "spline_batch_autotune", "spline_batch_count", "spline_batch_queued",
+            "spline_batch_destroy",
             "sp_conv3x3_fwd", "sp_conv3x3_bwd_data", "sp_conv3x3_bwd_weight", "sp_conv3x3_flip_weights")
 
 
@@ -104,6 +105,8 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
     lib.spline_batch_autotune.argtypes = [P, P, P, P, P]
     lib.spline_batch_count.restype = ctypes.c_int32
     lib.spline_batch_count.argtypes = [P]
+    lib.spline_batch_queued.restype = ctypes.c_int32
+    lib.spline_batch_queued.argtypes = [P, ctypes.c_int32]
     lib.spline_batch_destroy.restype = st
     lib.spline_batch_destroy.argtypes = [P]
     i32 = ctypes.c_int32
@@ -423,6 +426,11 @@ class Batch:
         paths = (ctypes.c_int32 * (2 * len(self)))()
         _check(load().spline_batch_autotune(self._h, self._ptrs(cs), self._ptrs(ps), _stream(stream), paths))
         return [(paths[2 * i], paths[2 * i + 1]) for i in range(len(self))]
+
+    def queued(self, adjoint: bool = False) -> int:
+        """Instances that the last recorded forward (or adjoint) graph runs
+        through the persistent work-queue kernel."""
+        return int(load().spline_batch_queued(self._h, 1 if adjoint else 0))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -566,6 +566,11 @@ struct sp_batch {
     cudaStream_t streams[kBatchStreams] = {};
     cudaEvent_t fork = nullptr, join[kBatchStreams] = {};
     GraphCache gfwd, gadj;
+    // strip-kernel instances run as one persistent launch over a work queue
+    spx::StripJob *jobs_dev[2] = {nullptr, nullptr};   // forward, adjoint
+    std::vector<spx::StripJob> jobs_host[2];
+    int64_t chunks[2] = {0, 0};
+    unsigned long long *counter = nullptr;              // [2]
 };
 
 }  // extern "C"
@@ -582,18 +587,23 @@ void batch_free(sp_batch *b)
     }
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (int d = 0; d < 2; ++d)
+        if (b->jobs_dev[d]) cudaFree(b->jobs_dev[d]);
+    if (b->counter) cudaFree(b->counter);
     for (sp_plan *p : b->plans) spline_plan_destroy(p);
     delete b;
 }
 
 // Fork the instances over the internal streams from `origin`, run op(i, s)
-// for instance i, and join back on `origin`.
-template <typename Op>
-cudaError_t fork_join(sp_batch *b, cudaStream_t origin, Op op)
+// for instance i and orig(origin) on the origin itself, and join back on
+// `origin`.
+template <typename Op, typename Orig>
+cudaError_t fork_join(sp_batch *b, cudaStream_t origin, Op op, Orig orig)
 {
     cudaError_t e = cudaEventRecord(b->fork, origin);
     for (int k = 0; k < kBatchStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->streams[k], b->fork, 0);
     for (size_t i = 0; i < b->plans.size() && e == cudaSuccess; ++i) e = op(i, b->streams[i % kBatchStreams]);
+    if (e == cudaSuccess) e = orig(origin);
     for (int k = 0; k < kBatchStreams && e == cudaSuccess; ++k) {
         e = cudaEventRecord(b->join[k], b->streams[k]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, b->join[k], 0);
@@ -601,15 +611,20 @@ cudaError_t fork_join(sp_batch *b, cudaStream_t origin, Op op)
     return e;
 }
 
-// Replay the cached graph for these pointers, or capture a new one.
-template <typename Op>
-cudaError_t run_graph(sp_batch *b, GraphCache &gc, const std::vector<const void *> &key, cudaStream_t s, Op op)
+// Replay the cached graph for these pointers, or capture a new one: set_up()
+// runs first (host side, outside the capture), then fork_join(op, orig) is
+// captured.
+template <typename Op, typename SetUp, typename Orig>
+cudaError_t run_graph(sp_batch *b, GraphCache &gc, const std::vector<const void *> &key, cudaStream_t s, Op op,
+                      SetUp set_up, Orig orig)
 {
     if (!gc.exec || gc.key != key) {
         gc.clear();
-        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = set_up();
         if (e != cudaSuccess) return e;
-        cudaError_t eop = fork_join(b, b->cap, op);
+        e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaError_t eop = fork_join(b, b->cap, op, orig);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(b->cap, &graph);
         if (eop != cudaSuccess) e = eop;
@@ -622,6 +637,51 @@ cudaError_t run_graph(sp_batch *b, GraphCache &gc, const std::vector<const void 
         gc.key = key;
     }
     return cudaGraphLaunch(gc.exec, s);
+}
+
+// Queue entries of the instances of direction d (0 forward, 1 adjoint) that
+// run on the strip kernels, uploaded to the batch's job array.  Runs outside
+// any capture; the device is synchronised first because a graph recorded
+// earlier may still read the previous array.
+template <typename In, typename Out>
+cudaError_t upload_jobs(sp_batch *b, int d, In in, Out outp, std::vector<char> &queued)
+{
+    std::vector<spx::StripJob> &hj = b->jobs_host[d];
+    hj.clear();
+    int64_t c0 = 0;
+    queued.assign(b->plans.size(), 0);
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        const sp_plan *p = b->plans[i];
+        const int path = d ? p->path_adj : p->path_fwd;
+        if (p->L.m == 0 || !use_strip(p->g, p->L, p->extra, path)) continue;
+        spx::StripJob J = d ? spx::make_strip_job(p->g, p->L, p->hdr, p->tabs, true, nullptr,
+                                                  const_cast<float *>(in[i]), outp[i], p->extra,
+                                                  slow_counter(p->g, p->extra))
+                            : spx::make_strip_job(p->g, p->L, p->hdr, p->tabs, false, in[i], outp[i], nullptr,
+                                                  p->extra, slow_counter(p->g, p->extra));
+        J.chunk0 = c0;
+        c0 += spx::strip_job_chunks(J);
+        hj.push_back(J);
+        queued[i] = 1;
+    }
+    b->chunks[d] = c0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && !hj.empty())
+        e = cudaMemcpy(b->jobs_dev[d], hj.data(), sizeof(spx::StripJob) * hj.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// The queued instances on the capture origin: per-instance set-up, the
+// persistent kernel, per-instance completion.
+cudaError_t run_queue(sp_batch *b, int d, cudaStream_t s)
+{
+    const std::vector<spx::StripJob> &hj = b->jobs_host[d];
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < hj.size() && e == cudaSuccess; ++k) e = spx::launch_strip_pre(hj[k], d == 1, s);
+    if (e == cudaSuccess)
+        e = spx::launch_strip_queue(d == 1, b->jobs_dev[d], (int)hj.size(), b->chunks[d], b->counter + d, s);
+    for (size_t k = 0; k < hj.size() && e == cudaSuccess; ++k) e = spx::launch_strip_post(hj[k], d == 1, s);
+    return e;
 }
 }  // namespace
 
@@ -647,6 +707,8 @@ sp_status spline_batch_create(int32_t count, const sp_grid *grids, const sp_line
     }
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int d = 0; d < 2 && e == cudaSuccess; ++d) e = cudaMalloc(&b->jobs_dev[d], sizeof(spx::StripJob) * (size_t)count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->counter, 2 * sizeof(unsigned long long));
     for (int k = 0; k < kBatchStreams && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
@@ -667,7 +729,7 @@ sp_status spline_batch_prepare(sp_batch *batch, void *stream)
     cudaError_t e = fork_join(batch, static_cast<cudaStream_t>(stream), [&](size_t i, cudaStream_t s) {
         st = spline_plan_prepare(batch->plans[i], s);
         return st == SP_OK ? cudaSuccess : cudaErrorUnknown;
-    });
+    }, [](cudaStream_t) { return cudaSuccess; });
     if (st != SP_OK) return st;
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "batch prepare");
 }
@@ -684,11 +746,16 @@ sp_status spline_batch_fwd(sp_batch *batch, const float *const *coef, float *con
         key.push_back(coef[i]);
         key.push_back(sino[i]);
     }
-    cudaError_t e = run_graph(batch, batch->gfwd, key, static_cast<cudaStream_t>(stream), [&](size_t i, cudaStream_t s) {
-        const sp_plan *p = batch->plans[i];
-        if (p->L.m == 0) return cudaSuccess;
-        return run_fwd(p->g, p->L, p->hdr, p->tabs, p->extra, coef[i], sino[i], s, p->path_fwd);
-    });
+    std::vector<char> queued;
+    cudaError_t e = run_graph(
+        batch, batch->gfwd, key, static_cast<cudaStream_t>(stream),
+        [&](size_t i, cudaStream_t s) {
+            const sp_plan *p = batch->plans[i];
+            if (p->L.m == 0 || queued[i]) return cudaSuccess;
+            return run_fwd(p->g, p->L, p->hdr, p->tabs, p->extra, coef[i], sino[i], s, p->path_fwd);
+        },
+        [&] { return upload_jobs(batch, 0, coef, sino, queued); },
+        [&](cudaStream_t s) { return run_queue(batch, 0, s); });
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "batch forward");
 }
 
@@ -704,10 +771,16 @@ sp_status spline_batch_adj(sp_batch *batch, const float *const *sino, float *con
         key.push_back(sino[i]);
         key.push_back(coef_out[i]);
     }
-    cudaError_t e = run_graph(batch, batch->gadj, key, static_cast<cudaStream_t>(stream), [&](size_t i, cudaStream_t s) {
-        const sp_plan *p = batch->plans[i];
-        return run_adj(p->g, p->L, p->hdr, p->tabs, p->extra, sino[i], coef_out[i], s, p->path_adj);
-    });
+    std::vector<char> queued;
+    cudaError_t e = run_graph(
+        batch, batch->gadj, key, static_cast<cudaStream_t>(stream),
+        [&](size_t i, cudaStream_t s) {
+            const sp_plan *p = batch->plans[i];
+            if (queued[i]) return cudaSuccess;
+            return run_adj(p->g, p->L, p->hdr, p->tabs, p->extra, sino[i], coef_out[i], s, p->path_adj);
+        },
+        [&] { return upload_jobs(batch, 1, sino, coef_out, queued); },
+        [&](cudaStream_t s) { return run_queue(batch, 1, s); });
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "batch adjoint");
 }
 
@@ -728,6 +801,12 @@ sp_status spline_batch_autotune(sp_batch *batch, const float *const *coef, const
 }
 
 int32_t spline_batch_count(const sp_batch *batch) { return batch ? (int32_t)batch->plans.size() : -1; }
+
+int32_t spline_batch_queued(const sp_batch *batch, int32_t adjoint)
+{
+    if (!batch) return -1;
+    return (int32_t)batch->jobs_host[adjoint ? 1 : 0].size();
+}
 
 sp_status spline_batch_destroy(sp_batch *batch)
 {

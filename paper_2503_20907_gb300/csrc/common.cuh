@@ -257,6 +257,36 @@ cudaError_t launch_fwd_strip(const GridDev &g, const LinesDev &L, const LineHdr 
 // Adjoint with strip accumulators; coef_out is overwritten.
 cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
                              const float *sino, void *scratch, float *coef_out, int *slow_rows, cudaStream_t s);
+
+// One instance of the persistent strip kernel's work queue: the arguments of
+// one strip projection and the index of its first chunk in the queue.
+struct StripJob {
+    GridDev g;
+    LinesDev L;
+    const LineHdr *hdr;
+    const float *tabs;
+    const float *coef;     // forward input (NULL for the adjoint)
+    float *coefT;          // scratch: transposed input (forward) ...
+    float *sino;
+    float *out, *outT;     // ... or output and transposed output (adjoint)
+    int *err;
+    int cpv;               // chunks per view
+    int vec;               // 16-byte staging and flushing
+    long long chunk0;
+};
+// The job of one strip projection (adj: img_out receives the adjoint of sino;
+// forward: sino receives the projection of img_in).  chunk0 is left 0.
+StripJob make_strip_job(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs, bool adj,
+                        const float *img_in, float *sino, float *img_out, void *scratch, int *err);
+int64_t strip_job_chunks(const StripJob &J);
+// Before the queue kernel: transposed copy of the input (forward) or cleared
+// outputs (adjoint); after it: the transposed output added in (adjoint).
+cudaError_t launch_strip_pre(const StripJob &J, bool adj, cudaStream_t s);
+cudaError_t launch_strip_post(const StripJob &J, bool adj, cudaStream_t s);
+// The persistent kernel over jobs[0..njobs) (device array, chunk0 ascending,
+// `total` chunks in all); counter is one device word, reset here.
+cudaError_t launch_strip_queue(bool adj, const StripJob *jobs, int njobs, int64_t total,
+                               unsigned long long *counter, cudaStream_t s);
 cudaError_t launch_footprint_eval(const GridDev &g, int64_t count, const float *theta, const float *yt,
                                   float *out, float *scratch, cudaStream_t s);
 

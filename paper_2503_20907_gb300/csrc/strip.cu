@@ -267,13 +267,16 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
 // Forward (ADJ false): sino[line] = h sum c phi.  Adjoint (ADJ true): adds
 // h sino[line] phi to out (vertical lines) or outT (horizontal lines, the
 // transposed image).
+// One chunk (view v, bins j0..j0+31) of one instance; smem is the CTA's
+// dynamic shared memory (kSmemBytes).
 template <int DEG, bool ADJ>
-__global__ void __launch_bounds__(kThreads, 2)
-strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
-             const float *__restrict__ coef, const float *__restrict__ coefT, float *__restrict__ sino,
-             float *__restrict__ out, float *__restrict__ outT, int chunks_per_view, int vec, int *err)
+__device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g, const LinesDev L,
+                                            const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
+                                            const float *__restrict__ coef, const float *__restrict__ coefT,
+                                            float *__restrict__ sino, float *__restrict__ out,
+                                            float *__restrict__ outT, int chunks_per_view, int vec, int *err,
+                                            int chunk)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
     float *strip = reinterpret_cast<float *>(smem);
     size_t o = kStripBytes;
     int *clo = reinterpret_cast<int *>(smem + o);
@@ -291,7 +294,7 @@ strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float
     float *tabbuf = reinterpret_cast<float *>(warp_area + warp * kWarpBytes);   // [2][kTabFloats]
     float *ent_t = reinterpret_cast<float *>(warp_area + warp * kWarpBytes + 2 * kTabBufBytes);
     int *ent_p = reinterpret_cast<int *>(ent_t + kEntCap);
-    const int v = blockIdx.x / chunks_per_view, cb = blockIdx.x - v * chunks_per_view;
+    const int v = chunk / chunks_per_view, cb = chunk - v * chunks_per_view;
     const int j0 = cb * kChunk;
     const int nl = min(kChunk, L.n_det - j0);
     const int64_t line0 = (int64_t)v * L.n_det + j0;
@@ -488,6 +491,58 @@ strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float
     }
 }
 
+template <int DEG, bool ADJ>
+__global__ void __launch_bounds__(kThreads, 2)
+strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
+             const float *__restrict__ coef, const float *__restrict__ coefT, float *__restrict__ sino,
+             float *__restrict__ out, float *__restrict__ outT, int chunks_per_view, int vec, int *err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    strip_chunk<DEG, ADJ>(smem, g, L, hdr, tabs, coef, coefT, sino, out, outT, chunks_per_view, vec, err,
+                          (int)blockIdx.x);
+}
+
+// Persistent kernel over the chunks of several instances: each CTA takes the
+// next chunk from one counter (atomicAdd; no CTA waits on another) and runs it
+// with its instance's parameters, until every chunk is taken.  Instance k
+// owns chunks [jobs[k].chunk0, jobs[k + 1].chunk0).
+template <bool ADJ>
+__global__ void __launch_bounds__(kThreads, 2)
+strip_queue_kernel(const StripJob *__restrict__ jobs, int njobs, long long total, unsigned long long *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long cur;
+    for (;;) {
+        __syncthreads();   // the previous chunk's last readers of shared memory are done
+        if (threadIdx.x == 0) cur = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long c = cur;
+        if (c >= total) break;
+        int lo = 0, hi = njobs - 1;   // last job whose first chunk is <= c
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].chunk0 <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const StripJob *J = jobs + lo;
+        const int local = (int)(c - J->chunk0);
+        switch (J->g.kdeg) {
+        case 1:
+            strip_chunk<1, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
+                                J->cpv, J->vec, J->err, local);
+            break;
+        case 2:
+            strip_chunk<2, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
+                                J->cpv, J->vec, J->err, local);
+            break;
+        default:
+            strip_chunk<3, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
+                                J->cpv, J->vec, J->err, local);
+            break;
+        }
+    }
+}
+
 __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int nx, int ny)
 {
     __shared__ float tile[32][33];
@@ -551,6 +606,73 @@ cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *h
 }
 
 }  // namespace
+
+StripJob make_strip_job(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs, bool adj,
+                        const float *img_in, float *sino, float *img_out, void *scratch, int *err)
+{
+    StripJob J;
+    J.g = g;
+    J.L = L;
+    J.hdr = hdr;
+    J.tabs = tabs;
+    J.coef = adj ? nullptr : img_in;
+    J.coefT = static_cast<float *>(scratch);
+    J.sino = sino;
+    J.out = adj ? img_out : nullptr;
+    J.outT = static_cast<float *>(scratch);
+    J.err = err;
+    J.cpv = (L.n_det + kChunk - 1) / kChunk;
+    const void *img = adj ? static_cast<const void *>(img_out) : static_cast<const void *>(img_in);
+    J.vec = (g.nx % 4 == 0) && (g.ny % 4 == 0) && ((reinterpret_cast<uintptr_t>(img) & 15) == 0) &&
+            ((reinterpret_cast<uintptr_t>(scratch) & 15) == 0);
+    J.chunk0 = 0;
+    return J;
+}
+
+int64_t strip_job_chunks(const StripJob &J) { return (int64_t)J.L.n_view * J.cpv; }
+
+cudaError_t launch_strip_pre(const StripJob &J, bool adj, cudaStream_t s)
+{
+    const dim3 tb(32, 8), tg((J.g.nx + 31) / 32, (J.g.ny + 31) / 32);
+    if (!adj) {
+        transpose_kernel<<<tg, tb, 0, s>>>(J.coef, J.coefT, J.g.nx, J.g.ny);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(J.out, 0, sizeof(float) * (size_t)J.g.nx * J.g.ny, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(J.outT, 0, sizeof(float) * (size_t)J.g.nx * J.g.ny, s);
+    return e;
+}
+
+cudaError_t launch_strip_post(const StripJob &J, bool adj, cudaStream_t s)
+{
+    if (!adj) return cudaSuccess;
+    const dim3 tb(32, 8), tg((J.g.nx + 31) / 32, (J.g.ny + 31) / 32);
+    add_transposed_kernel<<<tg, tb, 0, s>>>(J.outT, J.out, J.g.nx, J.g.ny);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strip_queue(bool adj, const StripJob *jobs, int njobs, int64_t total,
+                               unsigned long long *counter, cudaStream_t s)
+{
+    if (njobs <= 0 || total <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    int64_t grid = 2 * (int64_t)sms;   // two CTAs per SM, resident at once
+    if (grid > total) grid = total;
+    if (adj) {
+        e = cudaFuncSetAttribute(strip_queue_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e == cudaSuccess)
+            strip_queue_kernel<true><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(jobs, njobs, (long long)total, counter);
+    } else {
+        e = cudaFuncSetAttribute(strip_queue_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e == cudaSuccess)
+            strip_queue_kernel<false><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(jobs, njobs, (long long)total, counter);
+    }
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
 
 bool strip_supported(const GridDev &g, const LinesDev &L)
 {

@@ -50,6 +50,11 @@ def test_batch_matches_plans_and_replays(batch_setup):
     for bk, p, s in zip(backs, plans, sinos):
         ref = p.adj(s)
         assert float((bk - ref).norm() / ref.norm().clamp_min(1e-30)) < 1e-6
+    # the strip-eligible instances ran through the persistent queue kernel
+    n_strip = sum(1 for L, g in zip(lines, grids)
+                  if L.kind in (sp._lib.KIND_PARALLEL, sp._lib.KIND_FAN) and g.degree >= 1)
+    assert n_strip >= 2
+    assert batch.queued(False) == n_strip and batch.queued(True) == n_strip
 
 
 def test_batch_instances_match_oracle(batch_setup):
