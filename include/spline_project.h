@@ -243,9 +243,13 @@ sp_status spline_plan_autotune(sp_plan *plan, const float *coef, const float *si
  *   spline_batch_fwd      sino[i] = A_i coef[i] for every i; coef and sino
  *                         are HOST arrays of count DEVICE pointers
  *   spline_batch_adj      coef_out[i] = A_i^T sino[i]
- *   spline_batch_autotune spline_plan_autotune on each instance; paths
- *                         (NULL or host int32 [2 count]) receives the forward
- *                         and adjoint choice of each; drops recorded graphs
+ *   spline_batch_autotune spline_plan_autotune on each instance, then, per
+ *                         direction, the whole batch timed with those
+ *                         choices against the strip kernels wherever they
+ *                         apply (the faster is kept); paths (NULL or host
+ *                         int32 [2 count]) receives the forward and adjoint
+ *                         choice of each; uses temporary device buffers
+ *                         (cudaMalloc) for the outputs; drops recorded graphs
  *   spline_batch_destroy  frees everything (synchronises the device)
  * Calls on one batch must be ordered; capture of the graph needs the
  * device not to be capturing on the calling thread already.

@@ -789,14 +789,77 @@ sp_status spline_batch_autotune(sp_batch *batch, const float *const *coef, const
 {
     g_err.clear();
     if (!batch || !coef || !sino) return fail(SP_EINVAL, "NULL argument");
-    for (size_t i = 0; i < batch->plans.size(); ++i) {
-        int32_t f = 0, a = 0;
-        sp_status st = spline_plan_autotune(batch->plans[i], coef[i], sino[i], stream, &f, &a, nullptr);
+    const size_t cnt = batch->plans.size();
+    for (size_t i = 0; i < cnt; ++i) {
+        sp_status st = spline_plan_autotune(batch->plans[i], coef[i], sino[i], stream, nullptr, nullptr, nullptr);
         if (st != SP_OK) return fail(st, "instance " + std::to_string(i) + ": " + g_err);
-        if (paths) { paths[2 * i] = f; paths[2 * i + 1] = a; }
     }
+    // Whole batch: the instances' own choices against the strip kernels
+    // wherever they apply.  Inside the shared queue launch a small instance
+    // fills no GPU on its own, so timing it alone can understate the strip
+    // kernels.  Outputs go to temporary buffers.
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t ms_tot = 0, ns_tot = 0;
+    std::vector<char> eligible(cnt, 0);
+    for (size_t i = 0; i < cnt; ++i) {
+        const sp_plan *p = batch->plans[i];
+        ms_tot += align_up(sizeof(float) * (size_t)p->L.m);
+        ns_tot += align_up(sizeof(float) * (size_t)p->g.nx * p->g.ny);
+        eligible[i] = p->extra && spx::strip_supported(p->g, p->L) && p->L.m > 0;
+    }
+    char *tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, ms_tot + ns_tot);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    std::vector<float *> ts(cnt), tc(cnt);
+    {
+        size_t o = 0;
+        for (size_t i = 0; i < cnt; ++i) {
+            ts[i] = reinterpret_cast<float *>(tmp + o);
+            o += align_up(sizeof(float) * (size_t)batch->plans[i]->L.m);
+        }
+        for (size_t i = 0; i < cnt; ++i) {
+            tc[i] = reinterpret_cast<float *>(tmp + o);
+            o += align_up(sizeof(float) * (size_t)batch->plans[i]->g.nx * batch->plans[i]->g.ny);
+        }
+    }
+    sp_status st = SP_OK;
+    for (int d = 0; d < 2 && st == SP_OK && e == cudaSuccess; ++d) {
+        std::vector<int> own(cnt);
+        bool differs = false;
+        for (size_t i = 0; i < cnt; ++i) {
+            own[i] = d ? batch->plans[i]->path_adj : batch->plans[i]->path_fwd;
+            differs = differs || (eligible[i] && own[i] != kPathStrip);
+        }
+        if (!differs) continue;
+        float t[2] = {0.f, 0.f};   // own choices, strip wherever it applies
+        for (int v = 0; v < 2 && st == SP_OK && e == cudaSuccess; ++v) {
+            for (size_t i = 0; i < cnt; ++i) {
+                int &path = d ? batch->plans[i]->path_adj : batch->plans[i]->path_fwd;
+                path = (v == 1 && eligible[i]) ? kPathStrip : own[i];
+            }
+            batch->gfwd.clear();
+            batch->gadj.clear();
+            e = time_runs([&] {
+                st = d ? spline_batch_adj(batch, sino, tc.data(), stream)
+                       : spline_batch_fwd(batch, coef, ts.data(), stream);
+                return st == SP_OK ? cudaSuccess : cudaErrorUnknown;
+            }, 3, s, &t[v]);
+        }
+        if (st == SP_OK && e == cudaSuccess && t[0] <= t[1])
+            for (size_t i = 0; i < cnt; ++i) (d ? batch->plans[i]->path_adj : batch->plans[i]->path_fwd) = own[i];
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
     batch->gfwd.clear();
     batch->gadj.clear();
+    cudaFree(tmp);
+    if (st != SP_OK) return fail(st, "batch autotune: " + g_err);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+    if (paths)
+        for (size_t i = 0; i < cnt; ++i) {
+            paths[2 * i] = batch->plans[i]->path_fwd;
+            paths[2 * i + 1] = batch->plans[i]->path_adj;
+        }
     return SP_OK;
 }
 

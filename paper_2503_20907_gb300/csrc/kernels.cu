@@ -365,18 +365,30 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
                 if (lane == d) c = binomf(k, d);
             cb[k] = c;
         }
-        for (int pi = 1; pi < nh; ++pi) {
-            if (lane <= n) {
-                const int cur = bpq[pi], prev = bpq[pi - 1];
-                const float dl = sym_diff((cur & 255) - (prev & 255), (cur >> 8) - (prev >> 8), a, b, 0.f);
-                float sacc = 0.f;
-#pragma unroll
-                for (int k = nc - 1; k >= 0; --k)
-                    if (k >= lane) sacc = __fmaf_rn(sacc, dl, cb[k] * P[(pi - 1) * 8 + k]);
-                P[pi * 8 + lane] = sacc;
-            }
-            __syncwarp();
+        // lane pi holds the length of piece pi - 1 (the step to piece pi); the
+        // low coefficients of the previous piece travel in registers (lane d
+        // holds coefficient d), the top ones come from the scratch
+        float dlv = 0.f;
+        if (lane >= 1 && lane < nh) {
+            const int cur = bpq[lane], prev = bpq[lane - 1];
+            dlv = sym_diff((cur & 255) - (prev & 255), (cur >> 8) - (prev >> 8), a, b, 0.f);
         }
+        float low = 0.f;   // piece 0 starts the support: its coefficients 0..n vanish
+        for (int pi = 1; pi < nh; ++pi) {
+            const float dl = __shfl_sync(0xffffffffu, dlv, pi);
+            float c[nc];
+#pragma unroll
+            for (int k = 0; k <= n; ++k) c[k] = __shfl_sync(0xffffffffu, low, k);
+#pragma unroll
+            for (int k = n + 1; k < nc; ++k) c[k] = P[(pi - 1) * 8 + k];
+            float sacc = 0.f;
+#pragma unroll
+            for (int k = nc - 1; k >= 0; --k)
+                if (k >= lane) sacc = __fmaf_rn(sacc, dl, cb[k] * c[k]);
+            low = sacc;
+            if (lane <= n) P[pi * 8 + lane] = sacc;
+        }
+        __syncwarp();
         // u_0 interval ends s_q = (q b) mod a in (0, a], sorted (stable in q)
         float rq = 0.f;
         int fq = 0;
