@@ -275,7 +275,7 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
     float *sv = P + 25 * 8;                             // sorted u_0 interval ends
     int *sq = reinterpret_cast<int *>(sv + 8);
     int *sf = sq + 8;
-    for (int k = lane; k < kTabFloats; k += 32) tab[k] = 0.f;
+    for (int k = lane; k < kTabFloats / 4; k += 32) reinterpret_cast<float4 *>(tab)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncwarp();
     const float two_w = two_w_of(m, a, b);
     const float ainv = 1.0f / a;
@@ -298,14 +298,23 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
             q = lane - p * (m + 1);
             v = __fmaf_rn((float)p, a, (float)q * b);
         }
+        // all values in the scratch of the pieces (filled later), read back
+        // four at a time; ties go by index, which orders (p, q) lexicographically
+        float *vr = P;
+        if (lane < NB) vr[lane] = v;
+        __syncwarp();
         int rank = 0;
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            const float vj = __shfl_sync(0xffffffffu, v, j);
-            constexpr int M1 = m + 1;
-            const int pj = j / M1, qj = j - pj * M1;
-            rank += (vj < v) || (vj == v && (pj < p || (pj == p && qj < q)));
+        for (int j4 = 0; j4 < (NB + 3) / 4; ++j4) {
+            const float4 w4 = reinterpret_cast<const float4 *>(vr)[j4];
+            const float vj[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = 4 * j4 + u;
+                if (j < NB) rank += (vj[u] < v) || (vj[u] == v && j < lane);
+            }
         }
+        __syncwarp();
         if (lane < NB) { bv[rank] = v; bpq[rank] = p | (q << 8); }
         __syncwarp();
         // pieces that start at or before the centre w: the leading sorted run
@@ -433,9 +442,16 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
             const int bp = bpq[pi] & 255, bq = bpq[pi] >> 8;
             const float X = mirror ? sym_diff(m - pl - bp, m - ql - bq, a, b, 0.f) : sym_diff(pl - bp, ql - bq, a, b, 0.f);
             float *T = tab + tab_poly(sg, i);
-            float c[nc];
+            float c[8];
+            {
+                const float4 c0 = reinterpret_cast<const float4 *>(P + pi * 8)[0];
+                const float4 c1 = reinterpret_cast<const float4 *>(P + pi * 8)[1];
+                c[0] = c0.x; c[1] = c0.y; c[2] = c0.z; c[3] = c0.w;
+                c[4] = c1.x; c[5] = c1.y; c[6] = c1.z; c[7] = c1.w;
+            }
+            float r[8];
 #pragma unroll
-            for (int k = 0; k < nc; ++k) c[k] = P[pi * 8 + k];
+            for (int d = 0; d < 8; ++d) r[d] = 0.f;   // slots beyond nc stay zero
             if (X != 0.f) {
                 // Taylor shift of the piece to the interval start
 #pragma unroll
@@ -443,12 +459,14 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
                     float sacc = 0.f;
 #pragma unroll
                     for (int k = nc - 1; k >= d; --k) sacc = __fmaf_rn(sacc, X, binomf(k, d) * c[k]);
-                    T[d] = (mirror && (d & 1)) ? -sacc : sacc;
+                    r[d] = (mirror && (d & 1)) ? -sacc : sacc;
                 }
             } else {
 #pragma unroll
-                for (int d = 0; d < nc; ++d) T[d] = (mirror && (d & 1)) ? -c[d] : c[d];
+                for (int d = 0; d < nc; ++d) r[d] = (mirror && (d & 1)) ? -c[d] : c[d];
             }
+            reinterpret_cast<float4 *>(T)[0] = make_float4(r[0], r[1], r[2], r[3]);
+            reinterpret_cast<float4 *>(T)[1] = make_float4(r[4], r[5], r[6], r[7]);
         }
     }
     __syncwarp();
