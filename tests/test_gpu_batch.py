@@ -104,6 +104,60 @@ def test_general_and_strip_kernels_agree(batch_setup):
         assert float((b1 - b2).norm() / b2.norm()) < 1e-6
 
 
+def _mixed_instances():
+    """Edge cases of the queue: a chunk of fewer than 32 lines, one view, a
+    rectangular grid whose rows are not whole 16-byte chunks, degree 0 and a
+    free line list (both off the queue), a grid smaller than the support."""
+    rng = np.random.default_rng(77)
+    specs = []
+    # (grid, lines-maker)
+    specs.append((sp.Grid(37, 23, 3, 1.0), lambda: sp.Lines.fan(
+        torch.tensor([0.3], dtype=torch.float32, device=DEV), 90.0, 45.0, 5, -2.0, 1.0)))
+    specs.append((sp.Grid(50, 30, 2, 0.9, 1.5, -0.5), lambda: sp.Lines.parallel(
+        torch.from_numpy(np.sort(rng.uniform(0, np.pi, 13)).astype(np.float32)).to(DEV), 71, -35.0, 1.0)))
+    specs.append((sp.Grid(3, 3, 1, 1.0), lambda: sp.Lines.parallel(
+        torch.tensor([0.0, 0.7, 1.5707964], dtype=torch.float32, device=DEV), 9, -4.0, 1.0)))
+    specs.append((sp.Grid(40, 40, 0, 1.0), lambda: sp.Lines.parallel(
+        torch.linspace(0, 3.0, 17, device=DEV), 60, -30.0, 1.0)))
+    src, dst = workloads.random_lines_circle(700, 30.0, 5)
+    specs.append((sp.Grid(40, 40, 3, 1.0), lambda: sp.Lines.points(
+        torch.from_numpy(src).to(DEV), torch.from_numpy(dst).to(DEV))))
+    grids = [g for g, _ in specs]
+    lines = [mk() for _, mk in specs]
+    return grids, lines
+
+
+def test_batch_queue_edge_cases():
+    grids, lines = _mixed_instances()
+    batch = sp.Batch(grids, lines)
+    plans = [sp.Plan(g, L) for g, L in zip(grids, lines)]
+    gen = torch.Generator(device="cpu").manual_seed(11)
+    coefs = [torch.rand(g.ny, g.nx, generator=gen).to(DEV) for g in grids]
+    sinos = batch.fwd(coefs)
+    backs = batch.adj(sinos)
+    assert batch.queued(False) == 3 and batch.queued(True) == 3
+    for s, b, p, c, sn in zip(sinos, backs, plans, coefs, sinos):
+        assert torch.equal(s, p.fwd(c))
+        ref = p.adj(sn)
+        assert float((b - ref).norm() / ref.norm().clamp_min(1e-30)) < 1e-6
+    # only instances off the queue: nothing queued, same results
+    b2 = sp.Batch(grids[3:], lines[3:])
+    s2 = b2.fwd(coefs[3:])
+    assert b2.queued(False) == 0
+    for s, p, c in zip(s2, plans[3:], coefs[3:]):
+        assert torch.equal(s, p.fwd(c))
+    # one queued instance alone
+    b3 = sp.Batch(grids[:1], lines[:1])
+    s3 = b3.fwd(coefs[:1])
+    k3 = b3.adj(s3)
+    assert b3.queued(False) == 1 and b3.queued(True) == 1
+    assert torch.equal(s3[0], plans[0].fwd(coefs[0]))
+    ref = plans[0].adj(s3[0])
+    assert float((k3[0] - ref).norm() / ref.norm().clamp_min(1e-30)) < 1e-6
+    for b_ in (batch, b2, b3):
+        b_.close()
+
+
 def test_batch_invalid():
     with pytest.raises(sp.SplineError):
         sp.Batch([sp.Grid(8, 8, 5)], [sp.Lines.theta_y(torch.zeros(3, device=DEV), torch.zeros(3, device=DEV))])
