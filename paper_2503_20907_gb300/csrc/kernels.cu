@@ -41,9 +41,11 @@ __device__ __forceinline__ float factf(int n)
     return r;
 }
 
-// Unit direction (dx, dy) and a point (px, py) of line r, in double.
+// Unit direction (dx, dy) and a point (px, py) of line r, in double.  For
+// parallel and fan beams, vs / vc (if not NULL) hold sin and cos of the view
+// angle of line r, computed as below.
 __device__ void line_geometry(const LinesDev &L, int64_t r, double &dx, double &dy, double &px,
-                              double &py)
+                              double &py, const double *vs = nullptr, const double *vc = nullptr)
 {
     switch (L.kind) {
     case SP_LINES_THETA_Y: {
@@ -61,16 +63,18 @@ __device__ void line_geometry(const LinesDev &L, int64_t r, double &dx, double &
     }
     case SP_LINES_PARALLEL: {
         int64_t v = r / L.n_det, j = r - v * L.n_det;
-        double th = (double)L.view[v], s, c;
-        sincos(th, &s, &c);
+        double s, c;
+        if (vs) { s = *vs; c = *vc; }
+        else sincos((double)L.view[v], &s, &c);
         double yy = (double)L.det0 + (double)j * (double)L.ddet;
         dx = c; dy = s; px = yy * s; py = -yy * c;
         break;
     }
     default: {  // SP_LINES_FAN
         int64_t v = r / L.n_det, j = r - v * L.n_det;
-        double be = (double)L.view[v], sb, cb;
-        sincos(be, &sb, &cb);
+        double sb, cb;
+        if (vs) { sb = *vs; cb = *vc; }
+        else sincos((double)L.view[v], &sb, &cb);
         double sx = (double)L.dso * cb, sy = (double)L.dso * sb;
         double off = (double)L.det0 + (double)j * (double)L.ddet;
         double ex = -(double)L.dod * cb - off * sb, ey = -(double)L.dod * sb + off * cb;
@@ -145,12 +149,32 @@ __device__ void split_hi_lo(double x, int bits, float &hi, float &lo)
 }
 
 // ------------------------------------------------------------------ setup
-__global__ void setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, float *tabs, int64_t M)
+constexpr int kSetupThreads = 128;
+
+__global__ void __launch_bounds__(kSetupThreads) setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, float *tabs, int64_t M)
 {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // parallel and fan beams: sin and cos of each view once per block (the
+    // block's lines span at most blockDim.x views)
+    __shared__ double vsin[kSetupThreads], vcos[kSetupThreads];
+    const bool views = (L.kind == SP_LINES_PARALLEL || L.kind == SP_LINES_FAN);
+    int64_t v0 = 0;
+    if (views) {
+        const int64_t r0 = (int64_t)blockIdx.x * blockDim.x;
+        const int64_t r1 = min(r0 + (int64_t)blockDim.x, M) - 1;
+        v0 = r0 / L.n_det;
+        const int64_t nv = r1 / L.n_det - v0 + 1;
+        if (threadIdx.x < nv) sincos((double)L.view[v0 + threadIdx.x], &vsin[threadIdx.x], &vcos[threadIdx.x]);
+        __syncthreads();
+    }
     if (r >= M) return;
     double dx, dy, px, py;
-    line_geometry(L, r, dx, dy, px, py);
+    if (views) {
+        const int k = (int)(r / L.n_det - v0);
+        line_geometry(L, r, dx, dy, px, py, &vsin[k], &vcos[k]);
+    } else {
+        line_geometry(L, r, dx, dy, px, py);
+    }
     LineHdr H;
     H.U0_lo = 0.f;
     H.a_corr = 0.f;
@@ -258,16 +282,21 @@ __device__ __forceinline__ float sym_diff(int dp, int dq, float a, float b, floa
     return __fmaf_rn((float)dp, a, __fmaf_rn((float)dq, b, extra));
 }
 
-// Build the footprint table of one direction (see common.cuh), one warp per
-// table, degree N.  sm is this warp's shared scratch of kBuildScratch floats;
-// the table is assembled there and then written to out (if out is not NULL).
+// Build the footprint table of one direction (see common.cuh), degree N, on
+// one half-warp: l is the lane within the half (0..15) and gmask the half's
+// lanes.  sm is the half's shared scratch of kBuildScratch floats; the table
+// is assembled there and then written to out (if out is not NULL).  Every
+// phase fits 16 lanes (at most 15 pieces start before the centre of the
+// support; 25 breakpoints are ranked two per lane), so a warp builds two
+// tables at once.
 constexpr int kBuildScratch = kTabFloats + 32 + 32 + 25 * 8 + 8 + 8 + 8;
 constexpr int kTabWarps = 8;
 
 template <int N>
-__device__ void build_table_warp(float a, float b, float *out, float *sm, int lane)
+__device__ void build_table_half(float a, float b, float *out, float *sm, int l, unsigned gmask)
 {
     constexpr int n = N, m = N + 1, nc = 2 * N + 2;
+    constexpr int G = 16;
     float *tab = sm;
     float *bv = tab + kTabFloats;                       // sorted breakpoint values
     int *bpq = reinterpret_cast<int *>(bv + 32);        // and their (p, q), p | q << 8
@@ -275,15 +304,15 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
     float *sv = P + 25 * 8;                             // sorted u_0 interval ends
     int *sq = reinterpret_cast<int *>(sv + 8);
     int *sf = sq + 8;
-    for (int k = lane; k < kTabFloats / 4; k += 32) reinterpret_cast<float4 *>(tab)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncwarp();
+    for (int k = l; k < kTabFloats / 4; k += G) reinterpret_cast<float4 *>(tab)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp(gmask);
     const float two_w = two_w_of(m, a, b);
     const float ainv = 1.0f / a;
     if (b == 0.f) {
         // Dirac factor (Prop. 1): phi(u) = beta^n(u/a)/a on the a-knots.
-        if (lane < kTabHead) tab[lane] = lane == kTabA ? a : (lane == kTabB ? 0.f : (lane < m ? a : FLT_MAX));
-        if (lane < m * (n + 1)) {
-            const int i = lane / (n + 1), e = lane - i * (n + 1);
+        if (l < kTabHead) tab[l] = l == kTabA ? a : (l == kTabB ? 0.f : (l < m ? a : FLT_MAX));
+        if (l < m * (n + 1)) {
+            const int i = l / (n + 1), e = l - i * (n + 1);
             float sc = ainv;
             for (int k = 0; k < e; ++k) sc *= ainv;
             tab[tab_poly(0, i) + e] = kBPiece[n][i][e] * sc;
@@ -291,19 +320,27 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
     } else {
         // breakpoints p a + q b, ranked (ties by p, then q)
         constexpr int NB = (m + 1) * (m + 1);
-        int p = 0, q = 0;
-        float v = 0.f;
-        if (lane < NB) {
-            p = lane / (m + 1);
-            q = lane - p * (m + 1);
-            v = __fmaf_rn((float)p, a, (float)q * b);
-        }
+        constexpr int NI = (NB + G - 1) / G;   // breakpoints per lane: l and l + 16
         // all values in the scratch of the pieces (filled later), read back
         // four at a time; ties go by index, which orders (p, q) lexicographically
         float *vr = P;
-        if (lane < NB) vr[lane] = v;
-        __syncwarp();
-        int rank = 0;
+        int p[NI], q[NI];
+        float v[NI];
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int idx = l + G * it;
+            p[it] = 0; q[it] = 0; v[it] = 0.f;
+            if (idx < NB) {
+                p[it] = idx / (m + 1);
+                q[it] = idx - p[it] * (m + 1);
+                v[it] = __fmaf_rn((float)p[it], a, (float)q[it] * b);
+                vr[idx] = v[it];
+            }
+        }
+        __syncwarp(gmask);
+        int rank[NI];
+#pragma unroll
+        for (int it = 0; it < NI; ++it) rank[it] = 0;
 #pragma unroll
         for (int j4 = 0; j4 < (NB + 3) / 4; ++j4) {
             const float4 w4 = reinterpret_cast<const float4 *>(vr)[j4];
@@ -311,59 +348,72 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int j = 4 * j4 + u;
-                if (j < NB) rank += (vj[u] < v) || (vj[u] == v && j < lane);
+                if (j < NB)
+#pragma unroll
+                    for (int it = 0; it < NI; ++it)
+                        rank[it] += (vj[u] < v[it]) || (vj[u] == v[it] && j < l + G * it);
             }
         }
-        __syncwarp();
-        if (lane < NB) { bv[rank] = v; bpq[rank] = p | (q << 8); }
-        __syncwarp();
+        __syncwarp(gmask);
+#pragma unroll
+        for (int it = 0; it < NI; ++it)
+            if (l + G * it < NB) { bv[rank[it]] = v[it]; bpq[rank[it]] = p[it] | (q[it] << 8); }
+        __syncwarp(gmask);
         // pieces that start at or before the centre w: the leading sorted run
+        // (the last breakpoint, at 2w, is always beyond it)
         int mp = 0, mq = 0;
-        if (lane < NB) { mp = bpq[lane] & 255; mq = bpq[lane] >> 8; }
-        const unsigned outside =
-            __ballot_sync(0xffffffffu, lane >= NB || sym_diff(2 * mp - m, 2 * mq - m, a, b, 0.f) > 0.f);
-        int nh = __ffs(outside) - 1;   // lane NB at the latest (NB <= 25)
+        unsigned outside = 0u;
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int idx = l + G * it;
+            int ip = 0, iq = 0;
+            if (idx < NB) { ip = bpq[idx] & 255; iq = bpq[idx] >> 8; }
+            if (it == 0) { mp = ip; mq = iq; }
+            const unsigned bal = __ballot_sync(gmask, idx >= NB || sym_diff(2 * ip - m, 2 * iq - m, a, b, 0.f) > 0.f);
+            outside |= ((bal >> (threadIdx.x & 16)) & 0xFFFFu) << (G * it);
+        }
+        int nh = __ffs(outside) - 1;
         if (nh < 1) nh = 1;
         // derivatives n+1..2n+1 of every piece directly (right-sided at its start)
         const float binv = 1.0f / b;
         float am = 1.f;
 #pragma unroll
         for (int k = 0; k < m; ++k) am *= ainv;
-        if (lane < nh) {
+        if (l < nh) {
             const int p0 = mp, q0 = mq;
             float hi[n + 1];
 #pragma unroll
             for (int e = 0; e <= n; ++e) hi[e] = 0.f;
 #pragma unroll
             for (int pp = 0; pp <= m; ++pp) {
-                int l;
+                int piece;
                 float tau;
                 if (pp == p0) {
                     if (q0 >= m) continue;
-                    l = q0; tau = 0.f;
+                    piece = q0; tau = 0.f;
                 } else {
                     const float vv = __fmaf_rn((float)(p0 - pp), a, (float)q0 * b);
                     if (vv < 0.f) continue;
                     const float t = __fdiv_rn(vv, b);   // exact when vv is a multiple of b
-                    l = (int)floorf(t);
-                    if (l < 0 || l >= m) continue;
-                    tau = t - (float)l;
+                    piece = (int)floorf(t);
+                    if (piece < 0 || piece >= m) continue;
+                    tau = t - (float)piece;
                 }
                 float D[n + 1];
-                bspline_piece_derivs<n>(l, tau, binv, D);
+                bspline_piece_derivs<n>(piece, tau, binv, D);
                 const float wp = binomf(m, pp) * ((pp & 1) ? -1.f : 1.f);
 #pragma unroll
                 for (int e = 0; e <= n; ++e) hi[e] = __fmaf_rn(wp, D[e], hi[e]);
             }
 #pragma unroll
-            for (int e = 0; e <= n; ++e) P[lane * 8 + n + 1 + e] = hi[e] * am / factf(n + 1 + e);
-            if (lane == 0)
+            for (int e = 0; e <= n; ++e) P[l * 8 + n + 1 + e] = hi[e] * am / factf(n + 1 + e);
+            if (l == 0)
 #pragma unroll
                 for (int d = 0; d <= n; ++d) P[d] = 0.f;
         }
-        __syncwarp();
+        __syncwarp(gmask);
         // derivatives 0..n carried from piece to piece (lane d computes coefficient d);
-        // C(k, lane) held in registers (a lane-dependent index into a constant
+        // C(k, l) held in registers (a lane-dependent index into a constant
         // table would serialise the warp's constant loads)
         float cb[nc];
 #pragma unroll
@@ -371,57 +421,58 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
             float c = 0.f;
 #pragma unroll
             for (int d = 0; d <= n; ++d)
-                if (lane == d) c = binomf(k, d);
+                if (l == d) c = binomf(k, d);
             cb[k] = c;
         }
         // lane pi holds the length of piece pi - 1 (the step to piece pi); the
         // low coefficients of the previous piece travel in registers (lane d
         // holds coefficient d), the top ones come from the scratch
         float dlv = 0.f;
-        if (lane >= 1 && lane < nh) {
-            const int cur = bpq[lane], prev = bpq[lane - 1];
+        if (l >= 1 && l < nh) {
+            const int cur = bpq[l], prev = bpq[l - 1];
             dlv = sym_diff((cur & 255) - (prev & 255), (cur >> 8) - (prev >> 8), a, b, 0.f);
         }
         float low = 0.f;   // piece 0 starts the support: its coefficients 0..n vanish
         for (int pi = 1; pi < nh; ++pi) {
-            const float dl = __shfl_sync(0xffffffffu, dlv, pi);
+            const float dl = __shfl_sync(gmask, dlv, pi, G);
             float c[nc];
 #pragma unroll
-            for (int k = 0; k <= n; ++k) c[k] = __shfl_sync(0xffffffffu, low, k);
+            for (int k = 0; k <= n; ++k) c[k] = __shfl_sync(gmask, low, k, G);
 #pragma unroll
             for (int k = n + 1; k < nc; ++k) c[k] = P[(pi - 1) * 8 + k];
             float sacc = 0.f;
 #pragma unroll
             for (int k = nc - 1; k >= 0; --k)
-                if (k >= lane) sacc = __fmaf_rn(sacc, dl, cb[k] * c[k]);
+                if (k >= l) sacc = __fmaf_rn(sacc, dl, cb[k] * c[k]);
             low = sacc;
-            if (lane <= n) P[pi * 8 + lane] = sacc;
+            if (l <= n) P[pi * 8 + l] = sacc;
         }
-        __syncwarp();
+        __syncwarp(gmask);
         // u_0 interval ends s_q = (q b) mod a in (0, a], sorted (stable in q)
         float rq = 0.f;
         int fq = 0;
-        if (lane >= 1 && lane <= m) {
-            fq = (int)floorf((float)lane * b * ainv);
-            rq = __fmaf_rn((float)(-fq), a, (float)lane * b);
-            if (rq <= 0.f) { fq -= 1; rq = __fmaf_rn((float)(-fq), a, (float)lane * b); }
-            else if (rq > a) { fq += 1; rq = __fmaf_rn((float)(-fq), a, (float)lane * b); }
+        if (l >= 1 && l <= m) {
+            fq = (int)floorf((float)l * b * ainv);
+            rq = __fmaf_rn((float)(-fq), a, (float)l * b);
+            if (rq <= 0.f) { fq -= 1; rq = __fmaf_rn((float)(-fq), a, (float)l * b); }
+            else if (rq > a) { fq += 1; rq = __fmaf_rn((float)(-fq), a, (float)l * b); }
         }
         int srank = 1;
 #pragma unroll
         for (int j = 1; j <= m; ++j) {
-            const float rj = __shfl_sync(0xffffffffu, rq, j);
-            srank += (j < lane) ? (rj <= rq) : (j > lane ? (rj < rq) : 0);
+            const float rj = __shfl_sync(gmask, rq, j, G);
+            srank += (j < l) ? (rj <= rq) : (j > l ? (rj < rq) : 0);
         }
-        if (lane >= 1 && lane <= m) { sv[srank] = rq; sq[srank] = lane; sf[srank] = fq; }
-        if (lane == 0) { sv[0] = 0.f; sq[0] = 0; sf[0] = 0; }
-        __syncwarp();
-        if (lane < kTabHead) tab[lane] = lane == kTabA ? a : (lane == kTabB ? b : (lane < m ? sv[lane + 1] : FLT_MAX));
+        if (l >= 1 && l <= m) { sv[srank] = rq; sq[srank] = l; sf[srank] = fq; }
+        if (l == 0) { sv[0] = 0.f; sq[0] = 0; sf[0] = 0; }
+        __syncwarp(gmask);
+        if (l < kTabHead) tab[l] = l == kTabA ? a : (l == kTabB ? b : (l < m ? sv[l + 1] : FLT_MAX));
         const int K = slots_of(m, a, b, two_w);
-        // lane = (sigma, candidate) with candidate = lane % 8, four sigmas per pass
+        // entry e = (sigma, candidate) = (e / 8, e % 8), two sigmas per pass
 #pragma unroll
-        for (int pass = 0; pass < (m + 4) / 4; ++pass) {
-            const int sg = pass * 4 + (lane >> 3), i = lane & 7;
+        for (int pass = 0; pass < ((m + 1) * 8 + G - 1) / G; ++pass) {
+            const int e = l + G * pass;
+            const int sg = e >> 3, i = e & 7;
             if (sg > m || i >= K) continue;
             const float hw = 0.5f * (((sg < m) ? sv[sg + 1] : a) - sv[sg]);
             // interval start u_lo = (i - f) a + q b; midpoint u_lo + hw
@@ -469,11 +520,11 @@ __device__ void build_table_warp(float a, float b, float *out, float *sm, int la
             reinterpret_cast<float4 *>(T)[1] = make_float4(r[4], r[5], r[6], r[7]);
         }
     }
-    __syncwarp();
+    __syncwarp(gmask);
     if (out)
-        for (int k = lane; k < kTabFloats / 4; k += 32)
+        for (int k = l; k < kTabFloats / 4; k += G)
             reinterpret_cast<float4 *>(out)[k] = reinterpret_cast<const float4 *>(tab)[k];
-    __syncwarp();
+    __syncwarp(gmask);
 }
 
 // Table of the 3-direction box-spline (Sec. III.D), same layout as the
@@ -622,16 +673,30 @@ __device__ void build_table_box(float a, float b, int mode, float *out, float *s
 template <int DEG>
 __global__ void __launch_bounds__(kTabWarps * 32) tables_kernel(float *tabs, int64_t n_tab)
 {
-    __shared__ __align__(16) float scratch[kTabWarps][kBuildScratch];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * kTabWarps + warp;
-    if (t >= n_tab) return;
-    float *out = tabs + t * (int64_t)kTabFloats;
-    const float af = out[kTabA], bf = out[kTabB];
-    const int mode = (int)out[kTabMode];
+    __shared__ __align__(16) float scratch[2 * kTabWarps][kBuildScratch];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4;
+    const int64_t t0 = ((int64_t)blockIdx.x * kTabWarps + warp) * 2;
+    if (t0 >= n_tab) return;
+    const int nt = (t0 + 1 < n_tab) ? 2 : 1;
+    const int mode0 = (int)tabs[t0 * kTabFloats + kTabMode];
     __syncwarp();
-    if (DEG == 2 && mode != kModeBspline) build_table_box(af, bf, mode, out, scratch[warp], lane);
-    else build_table_warp<DEG>(af, bf, out, scratch[warp], lane);
+    if (DEG == 2 && mode0 != kModeBspline) {
+        // box-spline tables (one basis per grid, so both are): full warp each
+        for (int k = 0; k < nt; ++k) {
+            float *out = tabs + (t0 + k) * (int64_t)kTabFloats;
+            const float af = out[kTabA], bf = out[kTabB];
+            const int mode = (int)out[kTabMode];
+            __syncwarp();
+            if (mode != kModeBspline) build_table_box(af, bf, mode, out, scratch[2 * warp], lane);
+            else if (half == 0) build_table_half<DEG>(af, bf, out, scratch[2 * warp], lane, 0x0000FFFFu);
+            __syncwarp();
+        }
+        return;
+    }
+    if (half >= nt) return;
+    float *out = tabs + (t0 + half) * (int64_t)kTabFloats;
+    const float af = out[kTabA], bf = out[kTabB];
+    build_table_half<DEG>(af, bf, out, scratch[2 * warp + half], lane & 15, half ? 0xFFFF0000u : 0x0000FFFFu);
 }
 
 // ------------------------------------------------------------------ evaluation
@@ -851,7 +916,8 @@ __global__ void footprint_eval_kernel(int64_t count, const float *theta, const f
     footprint_ab(DEG, c, s, af, bf);
     const int mode = footprint_mode(basis, c, s);
     if (DEG == 2 && mode != kModeBspline) build_table_box(af, bf, mode, nullptr, scratch[warp], lane);
-    else build_table_warp<DEG>(af, bf, nullptr, scratch[warp], lane);
+    else if (lane < 16) build_table_half<DEG>(af, bf, nullptr, scratch[warp], lane, 0x0000FFFFu);
+    __syncwarp();
     if (lane == 0) out[r] = footprint_from_table<DEG>(scratch[warp], af, bf, mode, yt[r]);
 }
 
@@ -882,7 +948,7 @@ inline unsigned warp_blocks(int64_t lines)
 cudaError_t launch_setup(const GridDev &g, const LinesDev &L, LineHdr *hdr, float *tabs, cudaStream_t s)
 {
     if (L.m <= 0) return cudaSuccess;
-    setup_kernel<<<blocks_for(L.m, 128), 128, 0, s>>>(g, L, hdr, tabs, L.m);
+    setup_kernel<<<blocks_for(L.m, kSetupThreads), kSetupThreads, 0, s>>>(g, L, hdr, tabs, L.m);
     return cudaGetLastError();
 }
 
@@ -891,7 +957,7 @@ cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int6
 {
     (void)L;
     if (n_tab <= 0) return cudaSuccess;
-    SPX_DISPATCH(g.kdeg, tables_kernel, blocks_for(n_tab, kTabWarps), kTabWarps * 32, s, tabs, n_tab);
+    SPX_DISPATCH(g.kdeg, tables_kernel, blocks_for(n_tab, 2 * kTabWarps), kTabWarps * 32, s, tabs, n_tab);
     return cudaGetLastError();
 }
 
