@@ -668,7 +668,8 @@ __device__ void build_table_box(float a, float b, int mode, float *out, float *s
     __syncwarp();
 }
 
-// One warp per table.  a, b and the footprint kind were written into the
+// Two tables per warp, one per half-warp (box-spline tables: one after the
+// other on the full warp).  a, b and the footprint kind were written into the
 // table head by the line setup (FP64 geometry stays there, once per line).
 template <int DEG>
 __global__ void __launch_bounds__(kTabWarps * 32) tables_kernel(float *tabs, int64_t n_tab)
