@@ -61,15 +61,72 @@ def parse():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi sampled every 50 ms while the timed region runs."""
+    """SM clock and clock-event reasons while the timed region runs: NVML
+    queries (read-only, through ctypes) every 5 ms from a thread, else
+    nvidia-smi every 50 ms.  Only samples taken between start() and stop()
+    count."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8 | 0x80, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40}
 
     def __init__(self, index: int):
         self.index, self.proc, self.path = index, None, None
+        self.lib, self.handle, self.thread, self.rows, self.max_mhz = None, None, None, [], None
+        self._stop = False
+        self._open_nvml()
+
+    def _open_nvml(self):
+        import ctypes
+        lib = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None or lib.nvmlInit_v2() != 0:
+            return
+        h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.index)
+            bus = f"{pr.pci_domain_id:x}:{pr.pci_bus_id:x}:{pr.pci_device_id:x}.0".encode()
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) == 0
+        except Exception:
+            ok = False
+        if not ok:
+            ok = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) == 0
+        if not ok:
+            return
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) != 0:
+            return
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+        if self.reasons_fn is None:
+            return
+        self.lib, self.handle, self.max_mhz = lib, h, float(mx.value)
+
+    def _sample_loop(self):
+        import ctypes
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop:
+            if (self.lib.nvmlDeviceGetClockInfo(self.handle, ctypes.c_int(1), ctypes.byref(clk)) == 0 and
+                    self.reasons_fn(self.handle, ctypes.byref(rs)) == 0):
+                self.rows.append((float(clk.value), int(rs.value)))
+            time.sleep(0.005)
 
     def start(self):
+        if self.lib is not None:
+            import threading
+            self._stop = False
+            self.thread = threading.Thread(target=self._sample_loop, daemon=True)
+            self.thread.start()
+            return
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -80,6 +137,14 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self._stop = True
+            self.thread.join(timeout=5)
+            if not self.rows:
+                return None
+            reasons = sorted({k for _, r in self.rows for k, bit in self.BITS.items() if r & bit})
+            return {"sm_mhz": statistics.median(c for c, _ in self.rows), "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(self.rows), "source": "nvml, 5 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -102,7 +167,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi, 50 ms"}
 
 
 # ------------------------------------------------------------------ distributed
