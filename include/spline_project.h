@@ -208,8 +208,7 @@ sp_status spline_plan_cgls(sp_plan *plan, const float *b, float *x, int32_t iter
                            double *gamma_hist, void *stream);
 /*
  * Kernel choice of a plan, per direction: 0 = automatic (the strip kernels
- * for PARALLEL and FAN lines of kernel degree >= 1, else the general
- * kernels), 1 = strip kernels where they apply, 2 = general kernels
+ * for PARALLEL and FAN lines of degree >= 1, else the general kernels), 1 = strip kernels where they apply, 2 = general kernels
  * (warp per line).  Both give the same results within rounding (no paper
  * counterpart: this is an implementation choice).
  */
@@ -229,7 +228,8 @@ sp_status spline_plan_autotune(sp_plan *plan, const float *coef, const float *si
 /*
  * Batches: several independent instances (each its own grid, basis, degree
  * and line list, sizes free) projected together.  Instances on the strip
- * kernels (parallel and fan lists, degree >= 1, path not forced to the
+ * kernels (parallel and fan lists; degree >= 1 unless the path is set or
+ * tuned to them; path not forced to the
  * general kernels) share one persistent launch that takes chunks of 32
  * lines of any of them from a work queue; the others are forked over 8
  * internal streams; all are joined on the caller's stream.  The first call

@@ -151,14 +151,15 @@ int *slow_counter(const spx::GridDev &g, void *extra)
     return reinterpret_cast<int *>(static_cast<char *>(extra) + align_up(spx::strip_scratch_bytes(g)));
 }
 
-// Kernel paths: strip kernels (structured geometries, degree >= 1) or the
-// general warp-per-line kernels.  kPathAuto takes the strip kernels wherever
-// they apply.
+// Kernel paths: strip kernels (structured geometries, any degree) or the
+// general warp-per-line kernels.  kPathAuto takes the strip kernels for degree
+// >= 1 (at degree 0 a row has at most two candidates, too few to repay the
+// row records and their sort; the strip kernels run it when asked).
 enum KernelPath { kPathAuto = 0, kPathStrip = 1, kPathGeneral = 2 };
 
 bool use_strip(const spx::GridDev &g, const spx::LinesDev &L, void *extra, int path)
 {
-    return path != kPathGeneral && extra && spx::strip_supported(g, L);
+    return extra && spx::strip_supported(g, L) && (path == kPathStrip || (path == kPathAuto && g.kdeg >= 1));
 }
 
 // Forward projection.

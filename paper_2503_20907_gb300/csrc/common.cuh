@@ -248,7 +248,7 @@ cudaError_t launch_visited(const GridDev &g, const LineHdr *hdr, const float *ta
 cudaError_t launch_expand(const LinesDev &L, float *theta_out, float *y_out, cudaStream_t s);
 
 // Forward projection with coefficient strips in shared memory (strip.cu), for
-// parallel and fan beams of degree >= 1.  `scratch` holds strip_scratch_bytes;
+// parallel and fan beams (any degree).  `scratch` holds strip_scratch_bytes;
 // `slow_rows` counts rows whose run fell outside the staged window.
 bool strip_supported(const GridDev &g, const LinesDev &L);
 size_t strip_scratch_bytes(const GridDev &g);

@@ -113,6 +113,39 @@ __device__ __forceinline__ void table_copy_async(float *dst, const float *src, i
     for (int i = lane; i < kTabFloats / 4; i += 32) cp_async16(dst + 4 * i, src + 4 * i);
 }
 
+// Degree 0 exactly along an axis (kDeg0Axis): the footprint is a rectangle
+// whose edges fall on nodes, each taking the midpoint value on both sides, so
+// a row has one more candidate.  Such lines run lane per row straight from or
+// to global memory (as the general kernels do); they occur only at views
+// exactly along an axis.
+__device__ float strip_tie_line(const LineHdr &H, const float *tabw, int S0, int S1, int lane,
+                                const float *__restrict__ src, float *dst, int Nq, float hp, bool adj)
+{
+    const int sgn = (H.flags & kKapNeg) ? -1 : 1;
+    const float inv_a = 1.0f / H.a;
+    float s0[1] = {tabw[0]};
+    float acc = 0.f;
+    const int rb = max(H.r_begin, S0), re = min(H.r_end, S1);
+    for (int r = rb + lane; r < re; r += 32) {
+        const RowEval e = row_eval<0>(H, s0, inv_a, sgn, r);
+        for (int i = -1; i < H.K; ++i) {
+            const int q = e.q0 + sgn * i;
+            if ((unsigned)q >= (unsigned)Nq) continue;
+            float phi;
+            if (i < 0) {
+                if (!e.tie) continue;
+                phi = 0.5f * inv_a;   // the run also starts at u = 0
+            } else {
+                phi = horner<0>(tabw + tab_poly(e.sg, i), __fmaf_rn((float)i, H.a_corr, e.t));
+                if (e.tie) phi = 0.5f * phi;
+            }
+            if (adj) atomicAdd(dst + (size_t)r * Nq + q, hp * phi);
+            else acc = __fmaf_rn(__ldg(src + (size_t)r * Nq + q), phi, acc);
+        }
+    }
+    return acc;
+}
+
 // One line over the strip rows [S0, S1).  Forward (ADJ false): returns this
 // lane's part of sum_k c_k phi (no factor h).  Adjoint: adds hp * phi into the
 // strip.  tabw is the line's table in shared memory; ent_t / ent_p hold the
@@ -124,6 +157,8 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
 {
     constexpr int NC = 2 * DEG + 2;
     constexpr int NS = DEG + 2;       // intervals sigma
+    if constexpr (DEG == 0)
+        if (H.flags & kDeg0Axis) return strip_tie_line(H, tabw, S0, S1, lane, src, dst, Nq, hp, ADJ);
     const int sgn = (H.flags & kKapNeg) ? -1 : 1;
     const float inv_a = 1.0f / H.a;
     float s[DEG + 1];
@@ -171,7 +206,9 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
                     for (int i = 0; i < K; ++i) {
                         const int q = e.q0 + sgn * i;
                         if ((unsigned)q < (unsigned)Nq) {
-                            const float phi = horner<DEG>(T0 + i * kNC, e.t);
+                            // degree 0: candidate i sits i (|kappa| - a) further along u
+                            const float ti = (DEG == 0) ? __fmaf_rn((float)i, H.a_corr, e.t) : e.t;
+                            const float phi = horner<DEG>(T0 + i * kNC, ti);
                             if constexpr (ADJ) atomicAdd(dst + (size_t)r * Nq + q, hp * phi);
                             else acc_slow = __fmaf_rn(__ldg(src + (size_t)r * Nq + q), phi, acc_slow);
                         }
@@ -222,10 +259,16 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
                 const int n = segn[q];
                 if (n == 0) continue;
                 const float *Tq = tabw + tab_poly(q, ci);
+                float cq[NC];
+#pragma unroll
+                for (int d = 0; d < NC; ++d) cq[d] = Tq[d];
+                // degree 0: candidate ci's argument is t + ci (|kappa| - a);
+                // the linear polynomial takes the shift into its constant term
+                if constexpr (DEG == 0) cq[0] = __fmaf_rn(cq[1], (float)ci * H.a_corr, cq[0]);
                 f2 C[NC];
 #pragma unroll
                 for (int d = 0; d < NC; ++d) {
-                    const float c = ADJ ? Tq[d] * hp : Tq[d];
+                    const float c = ADJ ? cq[d] * hp : cq[d];
                     C[d] = f2pack(c, c);
                 }
                 const int end = segb[q] + n;
@@ -527,6 +570,10 @@ strip_queue_kernel(const StripJob *__restrict__ jobs, int njobs, long long total
         const StripJob *J = jobs + lo;
         const int local = (int)(c - J->chunk0);
         switch (J->g.kdeg) {
+        case 0:
+            strip_chunk<0, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
+                                J->cpv, J->vec, J->err, local);
+            break;
         case 1:
             strip_chunk<1, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
                                 J->cpv, J->vec, J->err, local);
@@ -676,7 +723,7 @@ cudaError_t launch_strip_queue(bool adj, const StripJob *jobs, int njobs, int64_
 
 bool strip_supported(const GridDev &g, const LinesDev &L)
 {
-    return (L.kind == SP_LINES_PARALLEL || L.kind == SP_LINES_FAN) && g.kdeg >= 1;
+    return (L.kind == SP_LINES_PARALLEL || L.kind == SP_LINES_FAN) && g.kdeg >= 0;
 }
 
 size_t strip_scratch_bytes(const GridDev &g) { return sizeof(float) * (size_t)g.nx * g.ny + 256; }
@@ -686,6 +733,7 @@ cudaError_t launch_fwd_strip(const GridDev &g, const LinesDev &L, const LineHdr 
 {
     float *coefT = static_cast<float *>(scratch);
     switch (g.kdeg) {
+    case 0: return launch_strip_t<0, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
     case 1: return launch_strip_t<1, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
     case 2: return launch_strip_t<2, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
     default: return launch_strip_t<3, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
@@ -698,6 +746,7 @@ cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr 
     float *outT = static_cast<float *>(scratch);
     float *p = const_cast<float *>(sino);
     switch (g.kdeg) {
+    case 0: return launch_strip_t<0, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);
     case 1: return launch_strip_t<1, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);
     case 2: return launch_strip_t<2, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);
     default: return launch_strip_t<3, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);

@@ -76,7 +76,7 @@ def test_autotune_choices_keep_parity(batch_setup):
     assert len(paths) == len(ws)
     for (f, a), L, g in zip(paths, lines, grids):
         assert f in (1, 2) and a in (1, 2)
-        if L.kind == sp._lib.KIND_POINTS or g.degree == 0:
+        if L.kind == sp._lib.KIND_POINTS:
             assert (f, a) == (2, 2)               # strip kernels do not apply
     out = batch.fwd(coefs)
     back = batch.adj(sinos)
@@ -91,7 +91,7 @@ def test_autotune_choices_keep_parity(batch_setup):
 def test_general_and_strip_kernels_agree(batch_setup):
     ws, grids, lines, coefs, batch, plans = batch_setup
     for p, c, L, g in zip(plans, coefs, lines, grids):
-        if L.kind not in (sp._lib.KIND_PARALLEL, sp._lib.KIND_FAN) or g.degree == 0:
+        if L.kind not in (sp._lib.KIND_PARALLEL, sp._lib.KIND_FAN):
             continue
         p.set_paths(1, 1)
         s1 = p.fwd(c)
@@ -107,7 +107,8 @@ def test_general_and_strip_kernels_agree(batch_setup):
 def _mixed_instances():
     """Edge cases of the queue: a chunk of fewer than 32 lines, one view, a
     rectangular grid whose rows are not whole 16-byte chunks, degree 0 and a
-    free line list (both off the queue), a grid smaller than the support."""
+    free line list (both off the queue by default), a grid smaller than the
+    support."""
     rng = np.random.default_rng(77)
     specs = []
     # (grid, lines-maker)
@@ -118,7 +119,7 @@ def _mixed_instances():
     specs.append((sp.Grid(3, 3, 1, 1.0), lambda: sp.Lines.parallel(
         torch.tensor([0.0, 0.7, 1.5707964], dtype=torch.float32, device=DEV), 9, -4.0, 1.0)))
     specs.append((sp.Grid(40, 40, 0, 1.0), lambda: sp.Lines.parallel(
-        torch.linspace(0, 3.0, 17, device=DEV), 60, -30.0, 1.0)))
+        torch.tensor([0.0, 0.4, 1.5707964, 2.2, 3.1415927], dtype=torch.float32, device=DEV), 60, -30.0, 1.0)))
     src, dst = workloads.random_lines_circle(700, 30.0, 5)
     specs.append((sp.Grid(40, 40, 3, 1.0), lambda: sp.Lines.points(
         torch.from_numpy(src).to(DEV), torch.from_numpy(dst).to(DEV))))
@@ -140,7 +141,8 @@ def test_batch_queue_edge_cases():
         assert torch.equal(s, p.fwd(c))
         ref = p.adj(sn)
         assert float((b - ref).norm() / ref.norm().clamp_min(1e-30)) < 1e-6
-    # only instances off the queue: nothing queued, same results
+    # only instances off the queue (degree 0 takes the general kernels unless
+    # tuned or set otherwise): nothing queued, same results
     b2 = sp.Batch(grids[3:], lines[3:])
     s2 = b2.fwd(coefs[3:])
     assert b2.queued(False) == 0

@@ -172,6 +172,32 @@ def test_degree0_axis_ties_midpoint():
     assert np.array_equal(counts.astype(np.int64), rc)
 
 
+@pytest.mark.parametrize("kind", ["parallel", "fan"])
+def test_degree0_on_strip_kernels(kind):
+    # degree 0 runs on the general kernels by default; set to the strip
+    # kernels (as the autotuner may) it keeps the parity bar, including the
+    # views exactly along an axis (midpoint rule, handled line by line)
+    g, og = _grid(40, 0)
+    if kind == "parallel":
+        view = np.array([0.0, 0.3, math.pi / 2, 1.9, 2.6], dtype=np.float32)
+        geo = workloads.Geometry("parallel", view_angle=view, n_det=70, det0=-34.5, ddet=1.0)
+    else:
+        geo = _small_geometry("fan", 0, 21)
+    coef = np.random.default_rng(5).uniform(-1, 1, (40, 40)).astype(np.float32)
+    lines = device_lines(geo, DEV)
+    th, yy = oracle_lines(geo)
+    plan = sp.Plan(g, lines)
+    plan.set_paths(1, 1)
+    sino = plan.fwd(torch.from_numpy(coef).to(DEV))
+    ref = oracle.forward(og, coef, th, yy)
+    assert rel_l2(sino.cpu().numpy(), ref) < TOL
+    p = np.random.default_rng(6).uniform(-1, 1, th.size).astype(np.float32)
+    back = plan.adj(torch.from_numpy(p).to(DEV)).cpu().numpy()
+    assert rel_l2(back, oracle.adjoint(og, p.astype(np.float64), th, yy)) < TOL
+    plan.set_paths(2, 2)
+    assert float((plan.fwd(torch.from_numpy(coef).to(DEV)) - sino).norm() / sino.norm()) < 1e-6
+
+
 def test_empty_and_missing_lines():
     g, og = _grid(20, 3)
     empty = sp.Lines.theta_y(torch.zeros(0, device=DEV), torch.zeros(0, device=DEV))
