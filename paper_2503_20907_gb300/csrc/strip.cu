@@ -258,10 +258,17 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
             for (int q = 0; q < NS; ++q) {
                 const int n = segn[q];
                 if (n == 0) continue;
-                const float *Tq = tabw + tab_poly(q, ci);
+                // T[sigma][ci]: 32-byte aligned (table buffers and entries are)
+                const float4 *Tq4 = reinterpret_cast<const float4 *>(tabw + tab_poly(q, ci));
                 float cq[NC];
 #pragma unroll
-                for (int d = 0; d < NC; ++d) cq[d] = Tq[d];
+                for (int d4 = 0; d4 < (NC + 3) / 4; ++d4) {
+                    const float4 w = Tq4[d4];
+                    const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (4 * d4 + u < NC) cq[4 * d4 + u] = wv[u];
+                }
                 // degree 0: candidate ci's argument is t + ci (|kappa| - a);
                 // the linear polynomial takes the shift into its constant term
                 if constexpr (DEG == 0) cq[0] = __fmaf_rn(cq[1], (float)ci * H.a_corr, cq[0]);
