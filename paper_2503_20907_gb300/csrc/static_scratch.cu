@@ -7,7 +7,7 @@
 // cannot afford the device-wide synchronisation that cudaFree (and growing a
 // cached workspace) implies.  spline_project_fwd_noalloc serves them: it runs
 // the same kernels as spline_project_fwd, but its scratch (per-line records
-// and footprint tables) lives in the fixed array below, which the driver sets
+// and footprint tables) lives in the fixed array below, which the CUDA driver sets
 // aside in every device's memory when the library is loaded and keeps until
 // the process exits.
 #include <mutex>
