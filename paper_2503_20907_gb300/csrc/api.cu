@@ -852,6 +852,10 @@ sp_status spline_batch_autotune(sp_batch *batch, const float *const *coef, const
     cudaError_t e2 = cudaStreamSynchronize(s);
     batch->gfwd.clear();
     batch->gadj.clear();
+    for (int d = 0; d < 2; ++d) {   // the timing runs' queues; the next call records anew
+        batch->jobs_host[d].clear();
+        batch->chunks[d] = 0;
+    }
     cudaFree(tmp);
     if (st != SP_OK) return fail(st, "batch autotune: " + g_err);
     if (e == cudaSuccess) e = e2;
