@@ -142,8 +142,8 @@ __device__ void split_hi_lo(double x, int bits, float &hi, float &lo)
     if (x == 0.0) { hi = 0.f; lo = 0.f; return; }
     int e;
     frexp(x, &e);
-    double sc = ldexp(1.0, bits - e);
-    double xh = rint(x * sc) / sc;
+    const double sc = ldexp(1.0, bits - e), isc = ldexp(1.0, e - bits);   // powers of two: exact
+    double xh = rint(x * sc) * isc;
     hi = (float)xh;
     lo = (float)(x - xh);
 }
