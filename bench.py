@@ -172,13 +172,18 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ distributed
 def dist_setup(n_gpus):
+    """One process per GPU under torch.distributed.run (NCCL); without a GPU
+    (the reference arm, or host-side tests) the ranks use gloo."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch
         import torch.distributed as dist
         local = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
         return dist.get_rank(), ws, local
     return 0, 1, 0
 
@@ -194,7 +199,8 @@ def allreduce_max(x: float, ws: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
