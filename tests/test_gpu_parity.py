@@ -208,6 +208,32 @@ def test_empty_and_missing_lines():
     assert float(sp.spline_project_fwd(g, coef, far).abs().max()) == 0.0
 
 
+@pytest.mark.parametrize("nx,ny,kind", [(2048, 2048, "fan"), (4096, 96, "parallel")])
+def test_large_grids_sampled(nx, ny, kind):
+    # grids beyond the benchmark's: index arithmetic over 4 M nodes, long
+    # major-axis rows, and a flat grid whose lines leave it after a few rows
+    n = 3
+    g, og = sp.Grid(nx, ny, n, 1.0), oracle.Grid(nx, ny, n, 1.0)
+    if kind == "fan":
+        geo = workloads.Geometry("fan", view_angle=np.linspace(0.05, 2 * math.pi, 12, endpoint=False).astype(np.float32),
+                                 n_det=3072, det0=-1535.5, ddet=1.0, dso=4000.0, dod=2000.0)
+    else:
+        geo = workloads.Geometry("parallel", view_angle=np.array([0.0, 0.2, 0.9, 1.5707964, 2.5], dtype=np.float32),
+                                 n_det=4200, det0=-2099.5, ddet=1.0)
+    rng = np.random.default_rng(nx + ny)
+    coef = rng.uniform(-1, 1, (ny, nx)).astype(np.float32)
+    lines = device_lines(geo, DEV)
+    th, yy = oracle_lines(geo)
+    plan = sp.Plan(g, lines)
+    sino = plan.fwd(torch.from_numpy(coef).to(DEV)).cpu().numpy()
+    idx = np.sort(rng.choice(th.size, 200, replace=False))
+    assert rel_l2(sino[idx], oracle.forward(og, coef, th[idx], yy[idx])) < TOL
+    p = rng.uniform(-1, 1, th.size).astype(np.float32)
+    back = plan.adj(torch.from_numpy(p).to(DEV)).cpu().numpy().ravel()
+    pix = np.sort(rng.choice(nx * ny, 16, replace=False))
+    assert rel_l2(back[pix], oracle.adjoint_pixels(og, p.astype(np.float64), th, yy, pix)) < TOL
+
+
 def test_tiny_and_rectangular_grids():
     for (nx, ny, n) in [(1, 1, 3), (1, 7, 2), (9, 1, 1), (3, 40, 3)]:
         g = sp.Grid(nx, ny, n, 1.3, 0.2, -0.4)
