@@ -193,10 +193,8 @@ sp_status prepare(const spx::GridDev &g, const spx::LinesDev &L, cudaStream_t s,
     *hdr = reinterpret_cast<spx::LineHdr *>(ws);
     *tabs = reinterpret_cast<float *>(static_cast<char *>(ws) + hb);
     if (extra) *extra = xb ? static_cast<char *>(ws) + hb + tb : nullptr;
-    cudaError_t e = spx::launch_setup(g, L, *hdr, *tabs, s);
-    if (e != cudaSuccess) return cuda_fail(e, "line setup");
-    e = spx::launch_tables(g, L, *tabs, nt, s);
-    if (e != cudaSuccess) return cuda_fail(e, "footprint tables");
+    cudaError_t e = spx::launch_prepare(g, L, *hdr, *tabs, nt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "line setup and footprint tables");
     return SP_OK;
 }
 
@@ -382,10 +380,8 @@ sp_status spline_plan_prepare(sp_plan *plan, void *stream)
     if (!plan) return fail(SP_EINVAL, "plan is NULL");
     if (plan->L.m == 0) { plan->prepared = true; return SP_OK; }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = spx::launch_setup(plan->g, plan->L, plan->hdr, plan->tabs, s);
-    if (e != cudaSuccess) return cuda_fail(e, "line setup");
-    e = spx::launch_tables(plan->g, plan->L, plan->tabs, table_count(plan->L), s);
-    if (e != cudaSuccess) return cuda_fail(e, "footprint tables");
+    cudaError_t e = spx::launch_prepare(plan->g, plan->L, plan->hdr, plan->tabs, table_count(plan->L), s);
+    if (e != cudaSuccess) return cuda_fail(e, "line setup and footprint tables");
     plan->prepared = true;
     return SP_OK;
 }

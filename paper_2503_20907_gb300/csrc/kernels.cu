@@ -151,43 +151,20 @@ __device__ void split_hi_lo(double x, int bits, float &hi, float &lo)
 // ------------------------------------------------------------------ setup
 constexpr int kSetupThreads = 128;
 
-__global__ void __launch_bounds__(kSetupThreads) setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, float *tabs, int64_t M)
+// Line setup of line r: its record hdr[r] (see LineHdr) and the footprint's
+// a, b and kind.  vs, vc: sin and cos of the line's view for parallel and fan
+// beams (NULL: computed here).
+__device__ void setup_line(const GridDev &g, const LinesDev &L, int64_t r, LineHdr *hdr, const double *vs,
+                           const double *vc, float &af, float &bf, int &mode)
 {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // parallel and fan beams: sin and cos of each view once per block (the
-    // block's lines span at most blockDim.x views)
-    __shared__ double vsin[kSetupThreads], vcos[kSetupThreads];
-    const bool views = (L.kind == SP_LINES_PARALLEL || L.kind == SP_LINES_FAN);
-    int64_t v0 = 0;
-    if (views) {
-        const int64_t r0 = (int64_t)blockIdx.x * blockDim.x;
-        const int64_t r1 = min(r0 + (int64_t)blockDim.x, M) - 1;
-        v0 = r0 / L.n_det;
-        const int64_t nv = r1 / L.n_det - v0 + 1;
-        if (threadIdx.x < nv) sincos((double)L.view[v0 + threadIdx.x], &vsin[threadIdx.x], &vcos[threadIdx.x]);
-        __syncthreads();
-    }
-    if (r >= M) return;
     double dx, dy, px, py;
-    if (views) {
-        const int k = (int)(r / L.n_det - v0);
-        line_geometry(L, r, dx, dy, px, py, &vsin[k], &vcos[k]);
-    } else {
-        line_geometry(L, r, dx, dy, px, py);
-    }
+    line_geometry(L, r, dx, dy, px, py, vs, vc);
     LineHdr H;
     H.U0_lo = 0.f;
     H.a_corr = 0.f;
     H.tab = (L.kind == SP_LINES_PARALLEL) ? (int)(r / L.n_det) : (int)r;
-    float af, bf;
     footprint_ab(g.kdeg, dx, dy, af, bf);
-    const int mode = footprint_mode(g.basis, dx, dy);
-    if (L.kind != SP_LINES_PARALLEL || r % L.n_det == 0) {
-        // the owner of table H.tab hands a, b and the footprint kind to the table builder
-        tabs[(int64_t)H.tab * kTabFloats + kTabA] = af;
-        tabs[(int64_t)H.tab * kTabFloats + kTabB] = bf;
-        tabs[(int64_t)H.tab * kTabFloats + kTabMode] = (float)mode;
-    }
+    mode = footprint_mode(g.basis, dx, dy);
     double w;
     support_params(g.kdeg, af, bf, mode, H.two_w, w, H.K);
     const bool vert = fabs(dy) >= fabs(dx);
@@ -252,6 +229,40 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(GridDev g, LinesDe
     H.r_end = re;
     H.flags = flags;
     hdr[r] = H;
+}
+
+__global__ void __launch_bounds__(kSetupThreads) setup_kernel(GridDev g, LinesDev L, LineHdr *hdr, float *tabs, int64_t M)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // parallel and fan beams: sin and cos of each view once per block (the
+    // block's lines span at most blockDim.x views)
+    __shared__ double vsin[kSetupThreads], vcos[kSetupThreads];
+    const bool views = (L.kind == SP_LINES_PARALLEL || L.kind == SP_LINES_FAN);
+    int64_t v0 = 0;
+    if (views) {
+        const int64_t r0 = (int64_t)blockIdx.x * blockDim.x;
+        const int64_t r1 = min(r0 + (int64_t)blockDim.x, M) - 1;
+        v0 = r0 / L.n_det;
+        const int64_t nv = r1 / L.n_det - v0 + 1;
+        if (threadIdx.x < nv) sincos((double)L.view[v0 + threadIdx.x], &vsin[threadIdx.x], &vcos[threadIdx.x]);
+        __syncthreads();
+    }
+        if (r >= M) return;
+    float af, bf;
+    int mode;
+    if (views) {
+        const int k = (int)(r / L.n_det - v0);
+        setup_line(g, L, r, hdr, &vsin[k], &vcos[k], af, bf, mode);
+    } else {
+        setup_line(g, L, r, hdr, nullptr, nullptr, af, bf, mode);
+    }
+    const int tab = (L.kind == SP_LINES_PARALLEL) ? (int)(r / L.n_det) : (int)r;
+    if (L.kind != SP_LINES_PARALLEL || r % L.n_det == 0) {
+        // the owner of table tab hands a, b and the footprint kind to the table builder
+        tabs[(int64_t)tab * kTabFloats + kTabA] = af;
+        tabs[(int64_t)tab * kTabFloats + kTabB] = bf;
+        tabs[(int64_t)tab * kTabFloats + kTabMode] = (float)mode;
+    }
 }
 
 // ------------------------------------------------------------------ tables
@@ -700,6 +711,54 @@ __global__ void __launch_bounds__(kTabWarps * 32) tables_kernel(float *tabs, int
     build_table_half<DEG>(af, bf, out, scratch[2 * warp + half], lane & 15, half ? 0xFFFF0000u : 0x0000FFFFu);
 }
 
+// Line setup and tables in one pass, for B-spline footprints with one table
+// per line (fan beams, point pairs, (theta, y) lists): each warp sets up 32
+// lines, one per lane (the FP64 geometry at full width), then builds their
+// 32 tables two at a time, one per half-warp.  Warps at the FP64 stage and
+// warps at the table stage share the SMs, so the two overlap.
+template <int DEG>
+__global__ void __launch_bounds__(kTabWarps * 32) setup_tables_kernel(GridDev g, LinesDev L, LineHdr *hdr, float *tabs,
+                                                                      int64_t M)
+{
+    __shared__ __align__(16) float scratch[2 * kTabWarps][kBuildScratch];
+    __shared__ double vsin[kTabWarps * 32], vcos[kTabWarps * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t r = r0 + threadIdx.x;
+    // fan beams: sin and cos of each view once per block (at most blockDim.x views)
+    const bool views = (L.kind == SP_LINES_FAN);
+    int64_t v0 = 0;
+    if (views) {
+        const int64_t r1 = min(r0 + (int64_t)blockDim.x, M) - 1;
+        v0 = r0 / L.n_det;
+        const int64_t nv = r1 / L.n_det - v0 + 1;
+        if (threadIdx.x < nv) sincos((double)L.view[v0 + threadIdx.x], &vsin[threadIdx.x], &vcos[threadIdx.x]);
+        __syncthreads();
+    }
+    float af = 0.f, bf = 0.f;
+    int mode = 0;
+    if (r < M) {
+        if (views) {
+            const int k = (int)(r / L.n_det - v0);
+            setup_line(g, L, r, hdr, &vsin[k], &vcos[k], af, bf, mode);
+        } else {
+            setup_line(g, L, r, hdr, nullptr, nullptr, af, bf, mode);
+        }
+    }
+    // the warp's 32 tables (table index = line index), two at a time
+    const int half = lane >> 4, hl = lane & 15;
+    const unsigned gmask = half ? 0xFFFF0000u : 0x0000FFFFu;
+    const int64_t rw = r0 + (int64_t)warp * 32;
+    for (int k = 0; k < 16; ++k) {
+        const int src = 2 * k + half;   // the lane that set up this half's line
+        const float a = __shfl_sync(0xffffffffu, af, src);
+        const float b = __shfl_sync(0xffffffffu, bf, src);
+        const int64_t rr = rw + src;
+        if (rr < M) build_table_half<DEG>(a, b, tabs + rr * kTabFloats, scratch[2 * warp + half], hl, gmask);
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------ evaluation
 // Visit every candidate of every row of one line; `op(node, phi)` is called
 // for in-grid candidates (phi may be 0 beyond the support).
@@ -951,6 +1010,21 @@ cudaError_t launch_setup(const GridDev &g, const LinesDev &L, LineHdr *hdr, floa
     if (L.m <= 0) return cudaSuccess;
     setup_kernel<<<blocks_for(L.m, kSetupThreads), kSetupThreads, 0, s>>>(g, L, hdr, tabs, L.m);
     return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(const GridDev &g, const LinesDev &L, LineHdr *hdr, float *tabs, int64_t n_tab,
+                           cudaStream_t s)
+{
+    if (L.m <= 0) return cudaSuccess;
+    if (g.basis == SP_BASIS_BSPLINE && L.kind != SP_LINES_PARALLEL) {
+        // one table per line: setup and tables in one kernel
+        SPX_DISPATCH(g.kdeg, setup_tables_kernel, blocks_for(L.m, kTabWarps * 32), kTabWarps * 32, s, g, L, hdr, tabs,
+                     L.m);
+        return cudaGetLastError();
+    }
+    cudaError_t e = launch_setup(g, L, hdr, tabs, s);
+    if (e == cudaSuccess) e = launch_tables(g, L, tabs, n_tab, s);
+    return e;
 }
 
 cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int64_t n_tab,
