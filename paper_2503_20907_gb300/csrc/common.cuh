@@ -239,7 +239,8 @@ cudaError_t launch_setup(const GridDev &g, const LinesDev &L, LineHdr *hdr, floa
 cudaError_t launch_tables(const GridDev &g, const LinesDev &L, float *tabs, int64_t n_tab,
                           cudaStream_t s);
 // Line setup and tables (one fused kernel where each line has its own
-// B-spline table, else launch_setup then launch_tables).
+// B-spline table and there are enough lines, else launch_setup then
+// launch_tables).
 cudaError_t launch_prepare(const GridDev &g, const LinesDev &L, LineHdr *hdr, float *tabs, int64_t n_tab,
                            cudaStream_t s);
 cudaError_t launch_fwd(const GridDev &g, const LineHdr *hdr, const float *tabs, int64_t m,

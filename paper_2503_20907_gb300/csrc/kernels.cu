@@ -1016,13 +1016,21 @@ cudaError_t launch_prepare(const GridDev &g, const LinesDev &L, LineHdr *hdr, fl
                            cudaStream_t s)
 {
     if (L.m <= 0) return cudaSuccess;
-    if (g.basis == SP_BASIS_BSPLINE && L.kind != SP_LINES_PARALLEL) {
-        // one table per line: setup and tables in one kernel
+    // one table per line: setup and tables in one kernel, where there are
+    // enough lines for warps at the FP64 stage and warps at the table stage to
+    // coexist (at least two waves of four 256-line blocks per SM; with fewer,
+    // all warps pass through both stages together and two kernels are faster)
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t wave = (int64_t)sms * 4 * kTabWarps * 32;
+    if (g.basis == SP_BASIS_BSPLINE && L.kind != SP_LINES_PARALLEL && L.m >= 2 * wave) {
         SPX_DISPATCH(g.kdeg, setup_tables_kernel, blocks_for(L.m, kTabWarps * 32), kTabWarps * 32, s, g, L, hdr, tabs,
                      L.m);
         return cudaGetLastError();
     }
-    cudaError_t e = launch_setup(g, L, hdr, tabs, s);
+    e = launch_setup(g, L, hdr, tabs, s);
     if (e == cudaSuccess) e = launch_tables(g, L, tabs, n_tab, s);
     return e;
 }
