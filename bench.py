@@ -206,10 +206,10 @@ def allreduce_max(x: float, ws: int) -> float:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(wl, seconds_hint: float = 1.0):
+def oracle_sample(wl, nf: int = 6000, npix: int = 160):
     """Time the FP64 oracle, as it stands, on a bounded sample of the
-    workload and scale to the full job: forward on a random subset of lines,
-    adjoint on a random subset of nodes (pixel-driven over every line)."""
+    workload and scale to the full job: forward on nf random lines, adjoint
+    on npix random nodes (pixel-driven over every line)."""
     import numpy as np
     import oracle
     geo = wl.geometry
@@ -217,13 +217,11 @@ def oracle_sample(wl, seconds_hint: float = 1.0):
                               geo.det0, geo.ddet)
     g = oracle.Grid(wl.n, wl.n, wl.degree, wl.h)
     rng = np.random.default_rng(7)
-    nf = 6000
     ridx = np.sort(rng.choice(th.size, nf, replace=False))
     t0 = time.perf_counter()
     oracle.forward(g, wl.coef, th[ridx], yy[ridx])
     tf = time.perf_counter() - t0
     p = rng.uniform(-1, 1, th.size)
-    npix = 160
     pix = np.sort(rng.choice(wl.n * wl.n, npix, replace=False))
     t0 = time.perf_counter()
     oracle.adjoint_pixels(g, p, th, yy, pix)
@@ -462,6 +460,8 @@ def run_ours(args, rank, ws, local):
                    "phantom": "30 seeded ellipses", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}"},
         "stage_ms": {"prepare": prep_ms, "fwd": fwd_ms, "adj": adj_ms},
+        "per_direction": {d: {"mrays_per_s": M / t / 1e3, "basis_evals_per_s": pairs / (t / 1000.0)}
+                          for d, t in (("fwd", fwd_ms), ("adj", adj_ms))},
         "pairs_per_direction": pairs,
         "slow_rows": slow_rows,
         "basis_evals_per_s": 2 * pairs * args.steps / (tot) if tot > 0 else None,
@@ -484,7 +484,7 @@ def run_ours(args, rank, ws, local):
     if warm is not None:
         line["warm_start"] = warm
     if ws == 1 and not args.no_cpu_baseline and wl.name == WORKLOAD:
-        cb = oracle_sample(wl)
+        cb = oracle_sample(wl, nf=120000, npix=1600)   # ~10 s on 16 host cores
         cb.pop("seconds", None)
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
