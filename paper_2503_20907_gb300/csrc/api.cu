@@ -650,7 +650,9 @@ cudaError_t upload_jobs(sp_batch *b, int d, In in, Out outp, std::vector<char> &
     for (size_t i = 0; i < b->plans.size(); ++i) {
         const sp_plan *p = b->plans[i];
         const int path = d ? p->path_adj : p->path_fwd;
-        if (p->L.m == 0 || !use_strip(p->g, p->L, p->extra, path)) continue;
+        // degree 0 (strip kernels only when set or tuned) keeps its own launch:
+        // the queue kernel carries degrees 1-3
+        if (p->L.m == 0 || p->g.kdeg < 1 || !use_strip(p->g, p->L, p->extra, path)) continue;
         spx::StripJob J = d ? spx::make_strip_job(p->g, p->L, p->hdr, p->tabs, true, nullptr,
                                                   const_cast<float *>(in[i]), outp[i], p->extra,
                                                   slow_counter(p->g, p->extra))

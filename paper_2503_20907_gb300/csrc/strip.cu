@@ -113,6 +113,63 @@ __device__ __forceinline__ void table_copy_async(float *dst, const float *src, i
     for (int i = lane; i < kTabFloats / 4; i += 32) cp_async16(dst + 4 * i, src + 4 * i);
 }
 
+// Phase B helpers of strip_line.  load_poly: the packed coefficients of
+// T[q][ci] (times hp for the adjoint; degree 0 with candidate ci's argument
+// shift ci (|kappa| - a) folded into the constant term).
+template <int DEG, bool ADJ>
+__device__ __forceinline__ void load_poly(const float *tabw, int q, int ci, float hp, float a_corr,
+                                          f2 (&C)[2 * DEG + 2])
+{
+    constexpr int NC = 2 * DEG + 2;
+    // T[sigma][ci]: 32-byte aligned (table buffers and entries are)
+    const float4 *Tq4 = reinterpret_cast<const float4 *>(tabw + tab_poly(q, ci));
+    float cq[NC];
+#pragma unroll
+    for (int d4 = 0; d4 < (NC + 3) / 4; ++d4) {
+        const float4 w = Tq4[d4];
+        const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (4 * d4 + u < NC) cq[4 * d4 + u] = wv[u];
+    }
+    if constexpr (DEG == 0) cq[0] = __fmaf_rn(cq[1], (float)ci * a_corr, cq[0]);
+#pragma unroll
+    for (int d = 0; d < NC; ++d) {
+        const float c = ADJ ? cq[d] * hp : cq[d];
+        C[d] = f2pack(c, c);
+    }
+}
+
+// run_group: the 4 sorted row records at e (one interval), two rows per packed
+// Horner chain; forward: acc2 += c phi from the strip; adjoint: reductions of
+// phi into the strip.
+template <int DEG, bool ADJ>
+__device__ __forceinline__ void run_group(const f2 (&C)[2 * DEG + 2], const float *ent_t, const int *ent_p, int e,
+                                          float *strip, int coloff, f2 &acc2)
+{
+    constexpr int NC = 2 * DEG + 2;
+    const ulonglong2 tt = *reinterpret_cast<const ulonglong2 *>(ent_t + e);
+    const int4 P = *reinterpret_cast<const int4 *>(ent_p + e);
+    f2 pa = C[NC - 1], pb = C[NC - 1];
+#pragma unroll
+    for (int d = NC - 2; d >= 0; --d) {
+        pa = f2fma(pa, tt.x, C[d]);
+        pb = f2fma(pb, tt.y, C[d]);
+    }
+    if constexpr (ADJ) {
+        float f0, f1, f2_, f3;
+        f2unpack(pa, f0, f1);
+        f2unpack(pb, f2_, f3);
+        red_shared(strip + P.x + coloff, f0);
+        red_shared(strip + P.y + coloff, f1);
+        red_shared(strip + P.z + coloff, f2_);
+        red_shared(strip + P.w + coloff, f3);
+    } else {
+        acc2 = f2fma(f2pack(strip[P.x + coloff], strip[P.y + coloff]), pa, acc2);
+        acc2 = f2fma(f2pack(strip[P.z + coloff], strip[P.w + coloff]), pb, acc2);
+    }
+}
+
 // Degree 0 exactly along an axis (kDeg0Axis): the footprint is a rectangle
 // whose edges fall on nodes, each taking the midpoint value on both sides, so
 // a row has one more candidate.  Such lines run lane per row straight from or
@@ -149,8 +206,9 @@ __device__ float strip_tie_line(const LineHdr &H, const float *tabw, int S0, int
 // One line over the strip rows [S0, S1).  Forward (ADJ false): returns this
 // lane's part of sum_k c_k phi (no factor h).  Adjoint: adds hp * phi into the
 // strip.  tabw is the line's table in shared memory; ent_t / ent_p hold the
-// warp's sorted row records (t, strip offset of candidate 0).
-template <int DEG, bool ADJ>
+// warp's sorted row records (t, strip offset of candidate 0).  CONCAT: the
+// adjoint's phase B schedule over the concatenated segments (below).
+template <int DEG, bool ADJ, bool CONCAT = ADJ>
 __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, int *ent_p, float *strip, const int *clo,
                             int S0, int S1, int lane, const float *__restrict__ src, float *dst, int Nq,
                             int *err, float hp)
@@ -254,52 +312,43 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
         __syncwarp();
         // ---- B: lane per (candidate, row slot), four rows per step
         if (lane_on) {
+            f2 C[NC];
+            if constexpr (ADJ && CONCAT) {
+                // The segments are contiguous and padded to whole groups of 4
+                // records, so slot sl takes groups sl, sl + nsl, ... of their
+                // concatenation (no slot idles at the end of a segment: each
+                // idle step would still cost its four reductions) and loads
+                // the polynomial of its group's interval on entering a segment.
+                const int R = segb[NS - 1] + segn[NS - 1];
+                int nb = 0;   // end of the segment whose polynomial is loaded
+                for (int e = 4 * sl; e < R; e += 4 * nsl) {
+                    if (e >= nb) {
+                        int q = 0, sb = 0, sn = 0;
 #pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                const int n = segn[q];
-                if (n == 0) continue;
-                // T[sigma][ci]: 32-byte aligned (table buffers and entries are)
-                const float4 *Tq4 = reinterpret_cast<const float4 *>(tabw + tab_poly(q, ci));
-                float cq[NC];
+                        for (int qq = 1; qq < NS; ++qq)
+                            if (segb[qq] <= e) q = qq;
 #pragma unroll
-                for (int d4 = 0; d4 < (NC + 3) / 4; ++d4) {
-                    const float4 w = Tq4[d4];
-                    const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (4 * d4 + u < NC) cq[4 * d4 + u] = wv[u];
-                }
-                // degree 0: candidate ci's argument is t + ci (|kappa| - a);
-                // the linear polynomial takes the shift into its constant term
-                if constexpr (DEG == 0) cq[0] = __fmaf_rn(cq[1], (float)ci * H.a_corr, cq[0]);
-                f2 C[NC];
-#pragma unroll
-                for (int d = 0; d < NC; ++d) {
-                    const float c = ADJ ? cq[d] * hp : cq[d];
-                    C[d] = f2pack(c, c);
-                }
-                const int end = segb[q] + n;
-                for (int e = segb[q] + 4 * sl; e < end; e += 4 * nsl) {
-                    const ulonglong2 tt = *reinterpret_cast<const ulonglong2 *>(ent_t + e);
-                    const int4 P = *reinterpret_cast<const int4 *>(ent_p + e);
-                    f2 pa = C[NC - 1], pb = C[NC - 1];
-#pragma unroll
-                    for (int d = NC - 2; d >= 0; --d) {
-                        pa = f2fma(pa, tt.x, C[d]);
-                        pb = f2fma(pb, tt.y, C[d]);
+                        for (int qq = 0; qq < NS; ++qq)
+                            if (qq == q) { sb = segb[qq]; sn = segn[qq]; }
+                        nb = sb + sn;
+                        load_poly<DEG, ADJ>(tabw, q, ci, hp, H.a_corr, C);
                     }
-                    if constexpr (ADJ) {
-                        float f0, f1, f2_, f3;
-                        f2unpack(pa, f0, f1);
-                        f2unpack(pb, f2_, f3);
-                        red_shared(strip + P.x + coloff, f0);
-                        red_shared(strip + P.y + coloff, f1);
-                        red_shared(strip + P.z + coloff, f2_);
-                        red_shared(strip + P.w + coloff, f3);
-                    } else {
-                        acc2 = f2fma(f2pack(strip[P.x + coloff], strip[P.y + coloff]), pa, acc2);
-                        acc2 = f2fma(f2pack(strip[P.z + coloff], strip[P.w + coloff]), pb, acc2);
-                    }
+                    run_group<DEG, ADJ>(C, ent_t, ent_p, e, strip, coloff, acc2);
+                }
+            } else {
+                // one interval at a time: the forward's steps are cheap enough
+                // that the per-step segment test of the schedule above costs
+                // more than the idle slots it saves (and the batch queue
+                // kernel, which carries every degree in one register budget,
+                // keeps this schedule for the adjoint too)
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    const int n = segn[q];
+                    if (n == 0) continue;
+                    load_poly<DEG, ADJ>(tabw, q, ci, hp, H.a_corr, C);
+                    const int end = segb[q] + n;
+                    for (int e = segb[q] + 4 * sl; e < end; e += 4 * nsl)
+                        run_group<DEG, ADJ>(C, ent_t, ent_p, e, strip, coloff, acc2);
                 }
             }
         }
@@ -319,7 +368,7 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
 // transposed image).
 // One chunk (view v, bins j0..j0+31) of one instance; smem is the CTA's
 // dynamic shared memory (kSmemBytes).
-template <int DEG, bool ADJ>
+template <int DEG, bool ADJ, bool CONCAT = ADJ>
 __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g, const LinesDev L,
                                             const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
                                             const float *__restrict__ coef, const float *__restrict__ coefT,
@@ -495,7 +544,7 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                     __syncwarp();
                     const LineHdr H = hdr_s[li];
                     const float hp = ADJ ? g.h * sino[line0 + li] : 0.f;
-                    const float part = strip_line<DEG, ADJ>(H, tabbuf + buf * kTabFloats, ent_t, ent_p, strip, clo, S0, S1,
+                    const float part = strip_line<DEG, ADJ, CONCAT>(H, tabbuf + buf * kTabFloats, ent_t, ent_p, strip, clo, S0, S1,
                                                             lane, src, dst, Nq, err, hp);
                     if (!ADJ) {
                         const float sum = warp_sum(part);
@@ -577,20 +626,16 @@ strip_queue_kernel(const StripJob *__restrict__ jobs, int njobs, long long total
         const StripJob *J = jobs + lo;
         const int local = (int)(c - J->chunk0);
         switch (J->g.kdeg) {
-        case 0:
-            strip_chunk<0, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
-                                J->cpv, J->vec, J->err, local);
-            break;
         case 1:
-            strip_chunk<1, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
+            strip_chunk<1, ADJ, false>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
                                 J->cpv, J->vec, J->err, local);
             break;
         case 2:
-            strip_chunk<2, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
+            strip_chunk<2, ADJ, false>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
                                 J->cpv, J->vec, J->err, local);
             break;
         default:
-            strip_chunk<3, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
+            strip_chunk<3, ADJ, false>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
                                 J->cpv, J->vec, J->err, local);
             break;
         }
