@@ -73,3 +73,17 @@ def test_host_side_argument_checks(lib):
     gu = L.SpGrid(8, 8, 1, 5, 1.0, 0.0, 0.0)          # unknown basis
     assert lib.spline_project_fwd(ctypes.byref(gu), 1, ctypes.byref(fan), 1, None) == L.SP_EINVAL
     assert lib.sp_version() >= 100
+
+
+def test_plan_and_batch_host_side_checks(lib):
+    from paper_2503_20907_gb300 import _lib as L
+    # NULL handles and bad counts are rejected before any CUDA call
+    assert lib.spline_batch_count(None) == -1
+    assert lib.spline_batch_queued(None, 0) == -1 and lib.spline_batch_queued(None, 1) == -1
+    h = ctypes.c_void_p()
+    assert lib.spline_batch_create(0, None, None, ctypes.byref(h)) == L.SP_EINVAL
+    assert lib.spline_batch_fwd(None, None, None, None) == L.SP_EINVAL
+    assert lib.spline_batch_adj(None, None, None, None) == L.SP_EINVAL
+    assert lib.spline_batch_autotune(None, None, None, None, None) == L.SP_EINVAL
+    assert lib.spline_batch_destroy(None) == L.SP_OK
+    assert lib.spline_plan_set_paths(None, 0, 0) == L.SP_EINVAL
