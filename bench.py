@@ -206,10 +206,11 @@ def allreduce_max(x: float, ws: int) -> float:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(wl, nf: int = 6000, npix: int = 160):
+def oracle_sample(wl, nf: int = 6000, npix: int = 160, threads: int = 0):
     """Time the FP64 oracle, as it stands, on a bounded sample of the
     workload and scale to the full job: forward on nf random lines, adjoint
-    on npix random nodes (pixel-driven over every line)."""
+    on npix random nodes (pixel-driven over every line); threads = 0: all
+    host cores."""
     import numpy as np
     import oracle
     geo = wl.geometry
@@ -219,16 +220,16 @@ def oracle_sample(wl, nf: int = 6000, npix: int = 160):
     rng = np.random.default_rng(7)
     ridx = np.sort(rng.choice(th.size, nf, replace=False))
     t0 = time.perf_counter()
-    oracle.forward(g, wl.coef, th[ridx], yy[ridx])
+    oracle.forward(g, wl.coef, th[ridx], yy[ridx], threads=threads)
     tf = time.perf_counter() - t0
     p = rng.uniform(-1, 1, th.size)
     pix = np.sort(rng.choice(wl.n * wl.n, npix, replace=False))
     t0 = time.perf_counter()
-    oracle.adjoint_pixels(g, p, th, yy, pix)
+    oracle.adjoint_pixels(g, p, th, yy, pix, threads=threads)
     ta = time.perf_counter() - t0
     m = th.size
     t_full = tf * m / nf + ta * (wl.n * wl.n) / npix
-    return {"value": m / t_full / 1e6, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+    return {"value": m / t_full / 1e6, "unit": UNIT, "cores": threads or oracle.max_threads(), "kind": "oracle",
             "sample": f"forward on {nf} of {m} lines ({tf:.2f} s), adjoint on {npix} of {wl.n * wl.n} nodes "
                       f"({ta:.2f} s), scaled to the full job ({t_full:.0f} s)",
             "seconds": tf + ta}
@@ -486,6 +487,8 @@ def run_ours(args, rank, ws, local):
     if ws == 1 and not args.no_cpu_baseline and wl.name == WORKLOAD:
         cb = oracle_sample(wl, nf=120000, npix=1600)   # ~10 s on 16 host cores
         cb.pop("seconds", None)
+        one = oracle_sample(wl, nf=4000, npix=60, threads=1)   # ~5 s on one core
+        cb["one_core"] = {"value": one["value"], "sample": one["sample"]}
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
 
