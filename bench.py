@@ -40,6 +40,8 @@ KERNELS_PER_STEP = 5   # line setup with tables (one fused kernel), transpose + 
 # kernels change until they are captured again.
 TRAFFIC = {"fan512_cubic": {"spline_fwd": 771186176, "spline_adj": 772421376}}   # re-captured after each kernel change
 CG_ITERS = 100
+CG_MAX_ITERS = 400   # cap of the run to the tolerance
+CG_TOL = 1e-4
 FLOPS_PER_PAIR = lambda n: 2 * (2 * n + 3)   # noqa: E731  (2n+1 Horner FMAs, 1 offset, 1 accumulate)
 
 
@@ -206,6 +208,37 @@ def allreduce_max(x: float, ws: int) -> float:
 
 
 # ------------------------------------------------------------------ CPU oracle
+def cpu_model() -> str:
+    """The host CPU's model name: lscpu's, else /proc/cpuinfo's "model name",
+    else its implementer and part codes (Arm), else the platform string."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                name = line.split(":", 1)[1].strip()
+                if name and name != "-":
+                    return name
+    except Exception:
+        pass
+    try:
+        impl = part = None
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            k, v = k.strip().lower(), v.strip()
+            if k == "model name" and v:
+                return v
+            if k == "cpu implementer":
+                impl = v
+            if k == "cpu part":
+                part = v
+        if impl or part:
+            return f"arm implementer {impl} part {part}"
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def oracle_sample(wl, nf: int = 6000, npix: int = 160, threads: int = 0):
     """Time the FP64 oracle, as it stands, on a bounded sample of the
     workload and scale to the full job: forward on nf random lines, adjoint
@@ -230,9 +263,47 @@ def oracle_sample(wl, nf: int = 6000, npix: int = 160, threads: int = 0):
     m = th.size
     t_full = tf * m / nf + ta * (wl.n * wl.n) / npix
     return {"value": m / t_full / 1e6, "unit": UNIT, "cores": threads or oracle.max_threads(), "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"forward on {nf} of {m} lines ({tf:.2f} s), adjoint on {npix} of {wl.n * wl.n} nodes "
                       f"({ta:.2f} s), scaled to the full job ({t_full:.0f} s)",
             "seconds": tf + ta}
+
+
+def cg_oracle_sample(sp, dev, n=64, iters=100):
+    """CPU baseline of the reconstruction step, and the GPU iterates against
+    it: FP64 oracle CGLS (100 iterations) on the 64 x 64 crop of the 512^2
+    cubic fan scan (transmission data, Poisson seed 3), timed on the host
+    cores; then the relative L2 error of each GPU iterate x_k (spline_plan_cgls
+    run k iterations from x_0 = 0) against the oracle's x_k, k = 1..100."""
+    import numpy as np
+    import torch
+    import oracle
+    from oracle.cgls import cgls
+    import workloads
+    W = workloads.crop_workload(workloads.workload(WORKLOAD), n)
+    geo = W.geometry
+    th, yy = oracle.lines_fan(geo.view_angle.astype(np.float64), geo.dso, geo.dod, geo.n_det, geo.det0, geo.ddet)
+    og = oracle.Grid(W.n, W.n, W.degree, W.h)
+    b, _ = workloads.transmission_data(oracle.forward(og, W.coef.astype(np.float64), th, yy), seed=3)
+    b32 = b.astype(np.float32)
+    t0 = time.perf_counter()
+    _, _, kept = cgls(lambda x: oracle.forward(og, x, th, yy), lambda p: oracle.adjoint(og, p, th, yy),
+                      b32.astype(np.float64), np.zeros((W.n, W.n)), iters, keep=range(1, iters + 1))
+    t_orc = time.perf_counter() - t0
+    plan = sp.Plan(sp.Grid(W.n, W.n, W.degree, W.h),
+                   sp.Lines.fan(torch.from_numpy(geo.view_angle).to(dev), geo.dso, geo.dod, geo.n_det,
+                                geo.det0, geo.ddet))
+    bt = torch.from_numpy(b32).to(dev)
+    err = []
+    for k in range(1, iters + 1):
+        x, _ = plan.cgls(bt, k, history=False)
+        ref = kept[k]
+        err.append(float(np.linalg.norm(x.cpu().numpy().astype(np.float64) - ref) / np.linalg.norm(ref)))
+    plan.close()
+    return {"workload": f"64x64 crop of {WORKLOAD} ({th.size} lines), transmission data, Poisson seed 3, x0 = 0",
+            "oracle_seconds_100_iters": t_orc, "cores": oracle.max_threads(),
+            "rel_err_vs_oracle_per_iter": [float(f"{e:.3g}") for e in err],
+            "max_rel_err_k_le_5": max(err[:5])}
 
 
 def run_reference(args, rank, ws):
@@ -253,7 +324,7 @@ def run_reference(args, rank, ws):
             "data": "synthetic", "config": {"workload": WORKLOAD, "grid": wl.n, "degree": wl.degree,
                                             "geometry": "fan 720 views x 768 bins, dso 1000, dod 500",
                                             "sample": "bounded sample per step, scaled to the full job"},
-            "cpu_baseline": {k: times[-1][k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "cpu_baseline": {k: times[-1][k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -305,7 +376,7 @@ def run_batch(args, sp, dev, stream, count=64):
     return out
 
 
-def run_warmstart(sp, dev, n_test=16, tol=1e-4):
+def run_warmstart(sp, dev, n_test=256, tol=1e-4):
     """Learned-vs-cold CGLS to a relative normal-equation residual of 1e-4 on
     held-out samples (256^2 cubic, parallel 360 x 384, Poisson data), with the
     committed network; times include the network's forward."""
@@ -426,17 +497,29 @@ def run_ours(args, rank, ws, local):
         b_cg = torch.from_numpy(b_np.astype(np.float32)).to(dev)
         plan.cgls(b_cg, 2)                       # allocates the plan's CG workspace
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        _, gam = plan.cgls(b_cg, CG_ITERS)
-        b.record(stream)
-        b.synchronize()
+
+        def timed_cgls(iters, history=True):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, gam = plan.cgls(b_cg, iters, history=history)
+            b.record(stream)
+            b.synchronize()
+            return a.elapsed_time(b), gam
+
+        ms100, gam = timed_cgls(CG_ITERS)
         g = gam.cpu().numpy()
+        # the same solve run on until the relative normal-equation residual
+        # reaches the tolerance, then timed for exactly that many iterations
+        _, gam_long = timed_cgls(CG_MAX_ITERS)
+        gl = gam_long.cpu().numpy()
+        k_tol = next((k for k in range(len(gl)) if np.sqrt(gl[k] / gl[0]) < CG_TOL), None)
+        ms_tol = timed_cgls(k_tol, history=False)[0] if k_tol else None
         cg = {"workload": f"{wl.name} transmission data (peak attenuation 3, I0 1e4, Poisson seed 3), x0 = 0",
-              "iters": CG_ITERS, "ms_per_iter": a.elapsed_time(b) / CG_ITERS,
+              "iters": CG_ITERS, "ms_per_iter": ms100 / CG_ITERS,
               "rel_residual_normal_eq": float(np.sqrt(g[-1] / g[0])),
-              "first_iter_rel_residual_below_1e-4": next((k for k in range(len(g)) if np.sqrt(g[k] / g[0]) < 1e-4),
-                                                         None),
+              "tol": CG_TOL, "iters_to_tol": k_tol, "ms_to_tol": ms_tol,
+              "rel_residual_at": {str(k): float(np.sqrt(gl[k] / gl[0])) for k in (10, 50, 100, 150, 200, 300)
+                                  if k < len(gl)},
               "kernels_per_iter": 8}
 
     batch = None if args.no_batch else run_batch(args, sp, dev, stream)
@@ -490,6 +573,8 @@ def run_ours(args, rank, ws, local):
         one = oracle_sample(wl, nf=4000, npix=60, threads=1)   # ~5 s on one core
         cb["one_core"] = {"value": one["value"], "sample": one["sample"]}
         line["cpu_baseline"] = cb
+        if cg is not None:
+            line["cg"]["vs_oracle_cgls"] = cg_oracle_sample(sp, dev)
     print(json.dumps(line), flush=True)
 
 

@@ -282,8 +282,10 @@ sp_status spline_plan_destroy(sp_plan *plan);
 
 /*
  * Forward projection that allocates nothing (this entry point has no
- * counterpart in the paper; it is the same computation as
- * spline_project_fwd).
+ * counterpart in the paper; it gives the same result as spline_project_fwd,
+ * always through the warp-per-line kernels: the strip kernels need a
+ * transposed image that the fixed scratch does not hold, so it runs at that
+ * path's speed, not at the strip path's).
  *
  * For callers that cannot let the library allocate device memory: programs
  * that reserve the device's memory up front for their own pool, where a
@@ -297,9 +299,14 @@ sp_status spline_plan_destroy(sp_plan *plan);
  * Limit: 64 bytes per line plus 1312 bytes per footprint table (one per line;
  * one per view for SP_LINES_PARALLEL) must fit in 48 MiB, i.e. about 36,000
  * lines with their own tables; larger lists return SP_EINVAL with the byte
- * count in sp_last_error().  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls on a device share the one array, and every call
+ * count in sp_last_error().  The first call with a nonempty line list on a
+ * device looks up the array's device address (cudaGetSymbolAddress); under
+ * lazy module loading (CUDA_MODULE_LOADING=LAZY, PyTorch's default) that
+ * lookup is also when the driver loads the array and reserves its 48 MiB on
+ * that device (and the kernels' code).  So make one such call first (a
+ * one-line list suffices), before the rest of the device memory goes to the
+ * caller's own pool and before any stream capture; later calls take no
+ * device memory.  All calls on a device share the one array, and every call
  * rewrites the part it uses before reading it: calls that overlap on the GPU
  * (other streams, or before the previous call's kernels finished) race.
  * Arguments, outputs and errors as spline_project_fwd.

@@ -5,11 +5,23 @@
 // caching allocator, a fixed-budget reconstruction service), where a foreign
 // cudaMalloc fails or fragments the pool, and latency-bound pipelines that
 // cannot afford the device-wide synchronisation that cudaFree (and growing a
-// cached workspace) implies.  spline_project_fwd_noalloc serves them: it runs
-// the same kernels as spline_project_fwd, but its scratch (per-line records
-// and footprint tables) lives in the fixed array below, which the CUDA driver sets
-// aside in every device's memory when the library is loaded and keeps until
-// the process exits.
+// cached workspace) implies.  spline_project_fwd_noalloc serves them.  It
+// gives the same result as spline_project_fwd, but always through the line
+// setup, table and warp-per-line forward kernels: the strip kernels that
+// spline_project_fwd takes for parallel and fan beams of degree >= 1 need a
+// transposed copy of the image, which the fixed array does not hold, so this
+// entry point runs at the speed of the warp-per-line path.  Its scratch
+// (per-line records and footprint tables) lives in the fixed array below.
+//
+// When that array takes device memory: the library is built without
+// relocatable device code, so the array sits in a module of its own, and
+// under lazy module loading (CUDA_MODULE_LOADING=LAZY, which PyTorch turns
+// on) the driver loads that module, and reserves the array's 48 MiB, only at
+// the first cudaGetSymbolAddress on a device, i.e. during the first call of
+// this entry point there.  That first call (a one-line list suffices) is
+// therefore the one step that takes device memory; callers make it before
+// they hand the rest of the device to their own pool and before any stream
+// capture.  From then on the array stays until the process exits.
 #include <mutex>
 #include <string>
 

@@ -39,14 +39,15 @@ def _case(sp, base, n):
 
 
 def test_autograd_project_gradcheck(sp):
-    W, plan, grid, th, y = _case(sp, "fan512_cubic", 12)
+    # the 32 x 32 crop of the 512^2 cubic fan scan (45 views x 48 bins, distances scaled)
+    W, plan, grid, th, y = _case(sp, "fan512_cubic", 32)
     c = torch.from_numpy(W.coef.astype(np.float32)).cuda().requires_grad_(True)
     assert torch.autograd.gradcheck(lambda x: sp.project(x, plan), (c,), eps=1e-2, atol=2e-3, rtol=1e-3,
                                     nondet_tol=1e-5)
 
 
 def test_autograd_backproject_gradcheck(sp):
-    W, plan, grid, th, y = _case(sp, "parallel256_cubic", 12)
+    W, plan, grid, th, y = _case(sp, "parallel256_cubic", 32)
     p = torch.randn(plan.m, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
     p.requires_grad_(True)
     assert torch.autograd.gradcheck(lambda s: sp.backproject(s, plan), (p,), eps=1e-2, atol=2e-3, rtol=1e-3,

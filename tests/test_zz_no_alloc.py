@@ -76,3 +76,45 @@ def test_noalloc_forward_refuses_lists_beyond_its_scratch():
     st = f(ctypes.byref(g), coef.data_ptr(), ctypes.byref(Lc), out.data_ptr(), None)
     assert st == L.SP_EINVAL
     assert b"scratch" in lib.sp_last_error()
+
+
+_FRESH = r"""
+import ctypes, math, sys
+import torch
+sys.path.insert(0, sys.argv[1])
+import paper_2503_20907_gb300 as sp
+from paper_2503_20907_gb300 import _lib as L
+lib = sp.load(build_if_stale=False)
+f = lib.spline_project_fwd_noalloc
+f.restype = ctypes.c_int
+f.argtypes = [ctypes.POINTER(L.SpGrid), ctypes.c_void_p, ctypes.POINTER(L.SpLines), ctypes.c_void_p, ctypes.c_void_p]
+dev = torch.device("cuda")
+grid = sp.Grid(64, 64, 3)
+lines = sp.Lines.fan(torch.linspace(0, 2 * math.pi, 121, device=dev)[:-1].contiguous(), 130.0, 65.0, 96, -47.5, 1.0)
+coef = torch.rand(64, 64, device=dev)
+out = torch.empty(lines.m, device=dev)
+g, Lc = grid.c(), lines.c()
+stream = torch.cuda.current_stream().cuda_stream
+# the first call on the device loads the array (and the kernels) under lazy module loading
+assert f(ctypes.byref(g), coef.data_ptr(), ctypes.byref(Lc), out.data_ptr(), stream) == 0, lib.sp_last_error()
+torch.cuda.synchronize()
+free0, _ = torch.cuda.mem_get_info()
+for _ in range(3):
+    assert f(ctypes.byref(g), coef.data_ptr(), ctypes.byref(Lc), out.data_ptr(), stream) == 0, lib.sp_last_error()
+torch.cuda.synchronize()
+free1, _ = torch.cuda.mem_get_info()
+print(free0, free1)
+assert free0 == free1, (free0, free1)
+"""
+
+
+def test_noalloc_forward_takes_no_device_memory_after_its_first_call():
+    """In a fresh process (no workspace left by earlier tests): after the first
+    call, further calls leave the device's free memory exactly as it was."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sp.load()   # build if needed before the child loads the library as it is
+    r = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
