@@ -489,19 +489,53 @@ def run_ours(args, rank, ws, local):
     h2d = coef_h.numel() * 4 + view_h.numel() * 4
     d2h = sino_h.numel() * 4 + back_h.numel() * 4
 
-    # CGLS on transmission data of the same scan (the reconstruction step)
+    # The same step with row records kept by the plan (written by prepare,
+    # read by both projections), as iterative solvers use it.
+    rec = None
+    plan_r = sp.Plan(grid, lines, prepare=True, records=True)
+    if plan_r.record_bytes() > 0:
+        def step_r(ev):
+            ev[0].record(stream)
+            plan_r.prepare(stream)
+            ev[1].record(stream)
+            plan_r.fwd(coef, sino, stream)
+            ev[2].record(stream)
+            plan_r.adj(sino, back, stream)
+            ev[3].record(stream)
+        evr = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        for k in range(3):
+            step_r(evr[0])
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            step_r(evr[k])
+        torch.cuda.synchronize()
+        rp_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evr)
+        rf_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evr)
+        ra_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evr)
+        rec = {"record_bytes": plan_r.record_bytes(),
+               "stage_ms": {"prepare": rp_ms, "fwd": rf_ms, "adj": ra_ms},
+               "mrays_per_s_step": M / ((rp_ms + rf_ms + ra_ms) / 1000.0) / 1e6,
+               "mrays_per_s_fwd_adj": M / ((rf_ms + ra_ms) / 1000.0) / 1e6}
+    else:
+        plan_r.close()
+        plan_r = None
+
+    # CGLS on transmission data of the same scan (the reconstruction step),
+    # on the plan with row records when it has them
     cg = None
     if not args.no_cg:
+        cgplan = plan_r if plan_r is not None else plan
         plan.fwd(coef, sino, stream)
         b_np, _ = workloads.transmission_data(sino.cpu().numpy(), seed=3)
         b_cg = torch.from_numpy(b_np.astype(np.float32)).to(dev)
-        plan.cgls(b_cg, 2)                       # allocates the plan's CG workspace
+        cgplan.cgls(b_cg, 2)                       # allocates the plan's CG workspace
         torch.cuda.synchronize()
 
         def timed_cgls(iters, history=True):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            _, gam = plan.cgls(b_cg, iters, history=history)
+            _, gam = cgplan.cgls(b_cg, iters, history=history)
             b.record(stream)
             b.synchronize()
             return a.elapsed_time(b), gam
@@ -520,7 +554,7 @@ def run_ours(args, rank, ws, local):
               "tol": CG_TOL, "iters_to_tol": k_tol, "ms_to_tol": ms_tol,
               "rel_residual_at": {str(k): float(np.sqrt(gl[k] / gl[0])) for k in (10, 50, 100, 150, 200, 300)
                                   if k < len(gl)},
-              "kernels_per_iter": 8}
+              "kernels_per_iter": 8, "row_records": cgplan.record_bytes() > 0}
 
     batch = None if args.no_batch else run_batch(args, sp, dev, stream)
     warm = None if args.no_warm else run_warmstart(sp, dev)
@@ -561,6 +595,8 @@ def run_ours(args, rank, ws, local):
         "clocks": clocks,
         "wall_s": wall,
     }
+    if rec is not None:
+        line["with_row_records"] = rec
     if cg is not None:
         line["cg"] = cg
     if batch is not None:

@@ -166,9 +166,19 @@ sp_status spline_visited(const sp_grid *grid, const sp_lines *lines, int32_t *co
  * (iterative reconstruction, autograd) skip the setup.  The steps of one pass
  * of the projector are then separate calls:
  *   spline_plan_prepare  line setup (eq. rayparam) and footprint tables
- *                        (Prop. 1, eq. xsa);
+ *                        (Prop. 1, eq. xsa), and, where the plan keeps
+ *                        them, the row records: for every major-axis row of
+ *                        every line, the position of its run of nodes and
+ *                        the argument of its footprint polynomials (the
+ *                        traversal of Algorithm 2), sorted by polynomial;
  *   spline_plan_fwd      forward projection (Algorithms 1-2);
  *   spline_plan_adj      adjoint.
+ * Row records (spline_plan_set_records) are for plans that project many
+ * times per prepare (iterative reconstruction): the projections then read
+ * them instead of recomputing the rows, with the same results (the forward
+ * bit for bit), at the price of a longer prepare and about 8 bytes per line
+ * and row of device memory (2.7 GB for 720 x 768 lines on a 512 x 512
+ * grid).  New plans keep none.
  * spline_plan_create allocates (cudaMalloc on the current device) and copies
  * the descriptors but enqueues no work; the device arrays that `lines` points
  * to must stay valid until the last spline_plan_prepare on the plan has run.
@@ -270,6 +280,18 @@ sp_status spline_batch_destroy(sp_batch *batch);
 
 /* Number of lines of the plan (-1 if plan is NULL). */
 int64_t spline_plan_lines(const sp_plan *plan);
+/* Device bytes of the plan's row records (0: the plan keeps none and its
+ * projections traverse the rows themselves; -1 if plan is NULL). */
+int64_t spline_plan_record_bytes(const sp_plan *plan);
+/*
+ * keep = 1: the plan keeps row records, written by every later
+ * spline_plan_prepare (the plan must be prepared again before it projects);
+ * SP_EUNSUPPORTED unless the lines are a parallel or fan beam and the degree
+ * is >= 1, SP_ENOMEM if they would take more than a quarter of the device's
+ * free memory or 16 GiB (cudaMalloc).  keep = 0 frees them (synchronises the
+ * device).
+ */
+sp_status spline_plan_set_records(sp_plan *plan, int32_t keep);
 /*
  * Diagnostics of the plan's forward projections so far (synchronises):
  * slow_rows = rows whose run of nodes fell outside the shared-memory window

@@ -44,7 +44,9 @@ class SplineError(RuntimeError):
 EXPORTED = ("sp_lines_count", "spline_project_fwd", "spline_project_adj", "spline_lines_expand",
             "spline_footprint_eval", "spline_visited", "sp_release_workspace", "sp_last_error",
             "sp_version", "spline_plan_create", "spline_plan_prepare", "spline_plan_fwd",
-            "spline_plan_adj", "spline_plan_lines", "spline_plan_destroy", "spline_plan_stats",
+            "spline_plan_adj", "spline_plan_lines", "spline_plan_record_bytes", "spline_plan_set_records",
+            "spline_plan_destroy",
+            "spline_plan_stats",
             "spline_project_fwd_noalloc", "spline_plan_cgls", "spline_plan_set_paths",
             "spline_plan_autotune", "spline_batch_create", "spline_batch_prepare", "spline_batch_fwd",
             "spline_batch_adj", "spline_batch_autotune", "spline_batch_count", "spline_batch_queued",
@@ -83,6 +85,10 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
     lib.spline_plan_adj.argtypes = [P, P, P, P]
     lib.spline_plan_lines.restype = ctypes.c_int64
     lib.spline_plan_lines.argtypes = [P]
+    lib.spline_plan_record_bytes.restype = ctypes.c_int64
+    lib.spline_plan_record_bytes.argtypes = [P]
+    lib.spline_plan_set_records.restype = st
+    lib.spline_plan_set_records.argtypes = [P, ctypes.c_int32]
     lib.spline_plan_stats.restype = st
     lib.spline_plan_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.spline_project_fwd_noalloc.restype = st
@@ -288,12 +294,14 @@ class Plan:
     """spline_plan_* wrapper: line records and footprint tables kept on the
     device for repeated projections with one (grid, lines) pair."""
 
-    def __init__(self, grid: Grid, lines: Lines, prepare: bool = True, stream=None):
+    def __init__(self, grid: Grid, lines: Lines, prepare: bool = True, stream=None, records: bool = False):
         self.grid, self.lines = grid, lines
         self._g, self._L = grid.c(), lines.c()
         h = ctypes.c_void_p()
         _check(load().spline_plan_create(ctypes.byref(self._g), ctypes.byref(self._L), ctypes.byref(h)))
         self._h = h
+        if records:
+            _check(load().spline_plan_set_records(self._h, 1))
         if prepare:
             self.prepare(stream)
 
@@ -359,6 +367,17 @@ class Plan:
         _check(load().spline_plan_autotune(self._h, c.data_ptr(), p.data_ptr(), _stream(stream),
                                            ctypes.byref(f), ctypes.byref(a), ms))
         return f.value, a.value, list(ms)
+
+    def set_records(self, keep: bool = True, stream=None):
+        """Keep row records (written by prepare, read by every projection) or
+        free them; prepares the plan again when they are kept."""
+        _check(load().spline_plan_set_records(self._h, 1 if keep else 0))
+        if keep:
+            self.prepare(stream)
+
+    def record_bytes(self) -> int:
+        """Device bytes of the row records the plan keeps (0: none)."""
+        return int(load().spline_plan_record_bytes(self._h))
 
     def slow_rows(self) -> int:
         """Rows read from global memory because they fell outside the staged window."""

@@ -162,22 +162,35 @@ bool use_strip(const spx::GridDev &g, const spx::LinesDev &L, void *extra, int p
     return extra && spx::strip_supported(g, L) && (path == kPathStrip || (path == kPathAuto && g.kdeg >= 1));
 }
 
-// Forward projection.
+// Forward projection (rec: the plan's row records, or NULL).
 cudaError_t run_fwd(const spx::GridDev &g, const spx::LinesDev &L, const spx::LineHdr *hdr, const float *tabs,
-                    void *extra, const float *coef, float *sino, cudaStream_t s, int path = kPathAuto)
+                    void *extra, const float *coef, float *sino, cudaStream_t s, int path = kPathAuto,
+                    const spx::StripRec *rec = nullptr)
 {
     if (use_strip(g, L, extra, path))
-        return spx::launch_fwd_strip(g, L, hdr, tabs, coef, extra, sino, slow_counter(g, extra), s);
+        return spx::launch_fwd_strip(g, L, hdr, tabs, coef, extra, sino, slow_counter(g, extra), s, rec);
     return spx::launch_fwd(g, hdr, tabs, L.m, coef, sino, s);
 }
 
 // Adjoint (coef_out overwritten).
 cudaError_t run_adj(const spx::GridDev &g, const spx::LinesDev &L, const spx::LineHdr *hdr, const float *tabs,
-                    void *extra, const float *sino, float *coef_out, cudaStream_t s, int path = kPathAuto)
+                    void *extra, const float *sino, float *coef_out, cudaStream_t s, int path = kPathAuto,
+                    const spx::StripRec *rec = nullptr)
 {
     if (use_strip(g, L, extra, path))
-        return spx::launch_adj_strip(g, L, hdr, tabs, sino, extra, coef_out, slow_counter(g, extra), s);
+        return spx::launch_adj_strip(g, L, hdr, tabs, sino, extra, coef_out, slow_counter(g, extra), s, rec);
     return spx::launch_adj(g, hdr, tabs, L.m, sino, coef_out, s);
+}
+
+// Row records a plan keeps: strip-path geometries of degree >= 1 (where the
+// strip kernels are the automatic choice), if they fit in a quarter of the
+// device's free memory and kRecMaxBytes.
+constexpr size_t kRecMaxBytes = size_t(16) << 30;
+
+size_t rec_bytes_wanted(const spx::GridDev &g, const spx::LinesDev &L)
+{
+    if (!spx::strip_supported(g, L) || g.kdeg < 1 || L.m == 0) return 0;
+    return (size_t)L.m * (size_t)spx::strip_rec_line_bytes(g);
 }
 
 sp_status prepare(const spx::GridDev &g, const spx::LinesDev &L, cudaStream_t s,
@@ -320,13 +333,38 @@ struct sp_plan {
     spx::LineHdr *hdr;
     float *tabs;
     void *extra;       // strip scratch (transposed coefficients, slow-row counter) or NULL
+    spx::StripRec rec; // row records written by prepare (base NULL: none)
     bool prepared;
     void *cg_ws;       // CGLS vectors and scalars, allocated on first use
     size_t cg_bytes;
     int path_fwd, path_adj;   // KernelPath of each direction
 };
 
-sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan **plan)
+}  // extern "C"
+
+namespace {
+// Row records for the plan if it can keep them (see rec_bytes_wanted); false
+// if it keeps none (the projections then traverse the rows themselves).
+bool plan_alloc_records(sp_plan *p)
+{
+    if (p->rec.base) return true;
+    const size_t rb = rec_bytes_wanted(p->g, p->L);
+    if (rb == 0) return false;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || rb > fr / 4 || rb > kRecMaxBytes) {
+        cudaGetLastError();
+        return false;
+    }
+    void *r = nullptr;
+    if (cudaMalloc(&r, rb) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    p->rec = spx::StripRec{static_cast<unsigned char *>(r), spx::strip_rec_line_bytes(p->g)};
+    return true;
+}
+
+sp_status plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan **plan, bool keep_records)
 {
     g_err.clear();
     if (!plan) return fail(SP_EINVAL, "plan is NULL");
@@ -362,6 +400,7 @@ sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan
     p->cg_ws = nullptr;
     p->cg_bytes = 0;
     p->path_fwd = p->path_adj = kPathAuto;
+    p->rec = spx::StripRec{nullptr, 0};
     if (p->extra) {
         e = cudaMemset(slow_counter(g, p->extra), 0, sizeof(int));
         if (e != cudaSuccess) {
@@ -370,7 +409,41 @@ sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan
             return cuda_fail(e, "cudaMemset");
         }
     }
+    if (keep_records) plan_alloc_records(p);
     *plan = p;
+    return SP_OK;
+}
+
+// The plan's row records, if it keeps them (written by every prepare).
+const spx::StripRec *plan_rec(const sp_plan *p) { return p->rec.base ? &p->rec : nullptr; }
+}  // namespace
+
+extern "C" {
+
+sp_status spline_plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan **plan)
+{
+    return plan_create(grid, lines, plan, false);
+}
+
+sp_status spline_plan_set_records(sp_plan *plan, int32_t keep)
+{
+    g_err.clear();
+    if (!plan) return fail(SP_EINVAL, "plan is NULL");
+    if (keep != 0 && keep != 1) return fail(SP_EINVAL, "keep must be 0 or 1");
+    if (keep == 0) {
+        if (plan->rec.base) {
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            cudaFree(plan->rec.base);
+            plan->rec = spx::StripRec{nullptr, 0};
+        }
+        return SP_OK;
+    }
+    if (plan->rec.base) return SP_OK;
+    if (rec_bytes_wanted(plan->g, plan->L) == 0)
+        return fail(SP_EUNSUPPORTED, "row records exist only for parallel and fan beams of degree >= 1");
+    if (!plan_alloc_records(plan)) return fail(SP_ENOMEM, "row records do not fit in device memory");
+    plan->prepared = false;   // records are written by the next prepare
     return SP_OK;
 }
 
@@ -382,6 +455,10 @@ sp_status spline_plan_prepare(sp_plan *plan, void *stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = spx::launch_prepare(plan->g, plan->L, plan->hdr, plan->tabs, table_count(plan->L), s);
     if (e != cudaSuccess) return cuda_fail(e, "line setup and footprint tables");
+    if (plan->rec.base) {
+        e = spx::launch_strip_record(plan->g, plan->L, plan->hdr, plan->tabs, plan->rec, s);
+        if (e != cudaSuccess) return cuda_fail(e, "row records");
+    }
     plan->prepared = true;
     return SP_OK;
 }
@@ -394,7 +471,7 @@ sp_status spline_plan_fwd(const sp_plan *plan, const float *coef, float *sino, v
     if (plan->L.m == 0) return SP_OK;
     if (!coef || !sino) return fail(SP_EINVAL, "coef/sino pointers are NULL");
     cudaError_t e = run_fwd(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, coef, sino,
-                            static_cast<cudaStream_t>(stream), plan->path_fwd);
+                            static_cast<cudaStream_t>(stream), plan->path_fwd, plan_rec(plan));
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "forward projection");
 }
 
@@ -406,7 +483,7 @@ sp_status spline_plan_adj(const sp_plan *plan, const float *sino, float *coef_ou
     if (!coef_out) return fail(SP_EINVAL, "coef_out pointer is NULL");
     if (plan->L.m > 0 && !sino) return fail(SP_EINVAL, "sino pointer is NULL");
     cudaError_t e = run_adj(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, sino, coef_out,
-                            static_cast<cudaStream_t>(stream), plan->path_adj);
+                            static_cast<cudaStream_t>(stream), plan->path_adj, plan_rec(plan));
     return e == cudaSuccess ? SP_OK : cuda_fail(e, "adjoint projection");
 }
 
@@ -414,12 +491,12 @@ namespace {
 cudaError_t plan_fwd_cb(void *ctx, const float *coef, float *sino, cudaStream_t s)
 {
     const sp_plan *p = static_cast<const sp_plan *>(ctx);
-    return run_fwd(p->g, p->L, p->hdr, p->tabs, p->extra, coef, sino, s, p->path_fwd);
+    return run_fwd(p->g, p->L, p->hdr, p->tabs, p->extra, coef, sino, s, p->path_fwd, plan_rec(p));
 }
 cudaError_t plan_adj_cb(void *ctx, const float *sino, float *coef_out, cudaStream_t s)
 {
     const sp_plan *p = static_cast<const sp_plan *>(ctx);
-    return run_adj(p->g, p->L, p->hdr, p->tabs, p->extra, sino, coef_out, s, p->path_adj);
+    return run_adj(p->g, p->L, p->hdr, p->tabs, p->extra, sino, coef_out, s, p->path_adj, plan_rec(p));
 }
 }  // namespace
 
@@ -456,6 +533,12 @@ sp_status spline_plan_cgls(sp_plan *plan, const float *b, float *x, int32_t iter
 }
 
 int64_t spline_plan_lines(const sp_plan *plan) { return plan ? plan->L.m : -1; }
+
+int64_t spline_plan_record_bytes(const sp_plan *plan)
+{
+    if (!plan) return -1;
+    return plan->rec.base ? plan->L.m * (int64_t)plan->rec.line_bytes : 0;
+}
 
 }  // extern "C"
 
@@ -696,7 +779,7 @@ sp_status spline_batch_create(int32_t count, const sp_grid *grids, const sp_line
     sp_batch *b = new sp_batch;
     for (int32_t i = 0; i < count; ++i) {
         sp_plan *p = nullptr;
-        sp_status st = spline_plan_create(grids + i, lines + i, &p);
+        sp_status st = plan_create(grids + i, lines + i, &p, false);
         if (st != SP_OK) {
             std::string msg = "instance " + std::to_string(i) + ": " + g_err;
             batch_free(b);
@@ -901,11 +984,12 @@ sp_status spline_plan_destroy(sp_plan *plan)
     g_err.clear();
     if (!plan) return SP_OK;
     sp_status st = SP_OK;
-    if (plan->mem || plan->cg_ws) {
+    if (plan->mem || plan->cg_ws || plan->rec.base) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) st = cuda_fail(e, "cudaDeviceSynchronize");
         if (plan->mem) cudaFree(plan->mem);
         if (plan->cg_ws) cudaFree(plan->cg_ws);
+        if (plan->rec.base) cudaFree(plan->rec.base);
     }
     delete plan;
     return st;

@@ -127,6 +127,25 @@ __device__ __forceinline__ float row_start(const LineHdr &H, float inv_a, int r,
     return u0;
 }
 
+// row_start for a row given as fr = (float)(r - r_ref) (exact): the step count
+// is carried as a float too, so the row costs one float-to-int conversion
+// (of k, returned) instead of four.  Same u_0 as row_start.
+__device__ __forceinline__ float row_start_f(const LineHdr &H, float inv_a, float fr, int &k)
+{
+    const float V = __fmaf_rn(fr, H.rho_hi + H.rho_lo, H.U0);
+    float fk = ceilf(V * inv_a) - 1.0f;
+    auto u0_of = [&](float kk) {
+        float big = __fsub_rn(__fmul_rn(fr, H.rho_hi), __fmul_rn(kk, H.a_hi));
+        float small = __fmaf_rn(fr, H.rho_lo, __fmul_rn(-kk, H.a_lo));
+        return __fadd_rn(__fadd_rn(H.U0, small), big);
+    };
+    float u0 = u0_of(fk);
+    if (u0 <= 0.0f) { fk -= 1.0f; u0 = u0_of(fk); }
+    else if (u0 > H.a) { fk += 1.0f; u0 = u0_of(fk); }
+    k = (int)fk;
+    return u0;
+}
+
 // Degree 0 near an axis has footprint ramps of width b, which can be far
 // narrower than one float ulp of u.  For that degree u_0 is carried as an
 // unevaluated sum hi + lo.
@@ -252,16 +271,31 @@ cudaError_t launch_visited(const GridDev &g, const LineHdr *hdr, const float *ta
                            cudaStream_t s);
 cudaError_t launch_expand(const LinesDev &L, float *theta_out, float *y_out, cudaStream_t s);
 
+// Sorted row records of every line, kept by a plan so that its projections
+// skip the per-row traversal (strip.cu): line_bytes per line, line-major.
+struct StripRec {
+    unsigned char *base;
+    long long line_bytes;
+};
+
 // Forward projection with coefficient strips in shared memory (strip.cu), for
 // parallel and fan beams (any degree).  `scratch` holds strip_scratch_bytes;
-// `slow_rows` counts rows whose run fell outside the staged window.
+// `slow_rows` counts rows whose run fell outside the staged window.  With
+// `rec` (written by launch_strip_record for the same lines) the row records
+// are read instead of recomputed.
 bool strip_supported(const GridDev &g, const LinesDev &L);
 size_t strip_scratch_bytes(const GridDev &g);
+long long strip_rec_line_bytes(const GridDev &g);
 cudaError_t launch_fwd_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
-                             const float *coef, void *scratch, float *sino, int *slow_rows, cudaStream_t s);
+                             const float *coef, void *scratch, float *sino, int *slow_rows, cudaStream_t s,
+                             const StripRec *rec = nullptr);
 // Adjoint with strip accumulators; coef_out is overwritten.
 cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
-                             const float *sino, void *scratch, float *coef_out, int *slow_rows, cudaStream_t s);
+                             const float *sino, void *scratch, float *coef_out, int *slow_rows, cudaStream_t s,
+                             const StripRec *rec = nullptr);
+// The row records of every line of (g, L) into rec (after line setup and tables).
+cudaError_t launch_strip_record(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
+                                const StripRec &rec, cudaStream_t s);
 
 // One instance of the persistent strip kernel's work queue: the arguments of
 // one strip projection and the index of its first chunk in the queue.

@@ -59,7 +59,9 @@ constexpr size_t kWarpBytes = 2 * kTabBufBytes + 2 * sizeof(float) * kEntCap;   
 constexpr size_t kAccBytes = sizeof(float) * kChunk;
 constexpr size_t kMiscBytes = 32 + 4 * 64;
 constexpr size_t kHdrBytes = sizeof(LineHdr) * kChunk;
-constexpr size_t kSmemBytes = kStripBytes + kCloBytes + kWarps * kWarpBytes + kAccBytes + kMiscBytes + kHdrBytes;
+constexpr size_t kRecOffBytes = sizeof(int) * kChunk;
+constexpr size_t kSmemBytes =
+    kStripBytes + kCloBytes + kWarps * kWarpBytes + kAccBytes + kMiscBytes + kHdrBytes + kRecOffBytes;
 static_assert(kTabBufBytes % 16 == 0 && kWarpBytes % 16 == 0 && kStripBytes % 16 == 0 && kCloBytes % 16 == 0,
               "16-byte alignment of the shared-memory regions");
 static_assert(kSmemBytes <= 115712, "two CTAs per SM");
@@ -106,6 +108,39 @@ constexpr int kFixMagicBits = 0x4B400000;
 constexpr float kFixMax = 2097152.0f;   // 2^21
 constexpr float kPhiBound = 1.5f;
 
+// Row records kept by a plan (see spline_plan_prepare): kRecWrite runs the
+// traversal (line groups, strip slabs, row batches, phase A and the sort) and
+// stores each batch's sorted records instead of projecting; kRecRead loads
+// them in the same order and runs phase B only.  Per line a region of
+// strip_rec_line_bytes(); per batch a 16-byte header (padded segment lengths,
+// and a flag for batches with runs outside the staged window, which the
+// replay recomputes), then t[R] and the strip offsets[R].
+enum RecMode { kRecNone = 0, kRecWrite = 1, kRecRead = 2 };
+constexpr unsigned long long kRecSlowBit = 1ull << 63;
+
+template <int NS>
+__device__ __forceinline__ int4 rec_pack(const int (&segn)[NS], bool slow)
+{
+    int n[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < NS; ++q) n[q] = segn[q];
+    return make_int4(n[0] | (n[1] << 16), n[2] | (n[3] << 16), n[4], slow ? (1 << 16) : 0);
+}
+
+template <int NS>
+__device__ __forceinline__ int rec_unpack(int4 hd, int (&segb)[NS], int (&segn)[NS])
+{
+    const int n[5] = {hd.x & 0xffff, hd.x >> 16, hd.y & 0xffff, hd.y >> 16, hd.z & 0xffff};
+    int b = 0;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        segb[q] = b;
+        segn[q] = n[q];
+        b += n[q];
+    }
+    return b;
+}
+
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
@@ -132,10 +167,17 @@ __device__ __forceinline__ void run_columns(const LineHdr &H, float inv_a, int r
     hi = max(q0, q1);
 }
 
-// Copy one footprint table (kTabFloats floats, 16-byte chunks) to shared memory.
-__device__ __forceinline__ void table_copy_async(float *dst, const float *src, int lane)
+// Copy the first n16 16-byte chunks of a footprint table (all kTabFloats / 4
+// of them, or its head alone) to shared memory.
+__device__ __forceinline__ void table_copy_async(float *dst, const float *src, int lane, int n16 = kTabFloats / 4)
 {
-    for (int i = lane; i < kTabFloats / 4; i += 32) cp_async16(dst + 4 * i, src + 4 * i);
+    for (int i = lane; i < n16; i += 32) cp_async16(dst + 4 * i, src + 4 * i);
+}
+
+// Prefetch `bytes` from p towards L2 (one 128-byte line per lane and pass).
+__device__ __forceinline__ void prefetch_span_l2(const unsigned char *p, int bytes, int lane)
+{
+    for (int o = lane * 128; o < bytes; o += 32 * 128) prefetch_l2(p + o);
 }
 
 // Phase B helpers of strip_line.  load_poly: the packed coefficients of
@@ -243,11 +285,12 @@ __device__ float strip_tie_line(const LineHdr &H, const float *tabw, int S0, int
 // strip.  tabw is the line's table in shared memory; ent_t / ent_p hold the
 // warp's sorted row records (t, strip offset of candidate 0).  CONCAT: the
 // adjoint's phase B schedule over the concatenated segments (below).
-template <int DEG, bool ADJ, bool CONCAT = ADJ, bool FIX = false>
+template <int DEG, bool ADJ, bool CONCAT = ADJ, bool FIX = false, int RM = kRecNone>
 __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, int *ent_p, float *strip, const int *clo,
                             int S0, int S1, int lane, const float *__restrict__ src, float *dst, int Nq,
-                            int *err, float hp, float hpS)
+                            int *err, float hp, float hpS, unsigned char *&rp, const unsigned char *rend)
 {
+    constexpr int rmode = RM;
     constexpr int NC = 2 * DEG + 2;
     constexpr int NS = DEG + 2;       // intervals sigma
     if constexpr (DEG == 0)
@@ -271,10 +314,31 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
     const int dummy_pos = kSlabRows * kPitch + kDummy / 2;
     const int rb = max(H.r_begin, S0), re = min(H.r_end, S1);
     for (int r0 = rb; r0 < re; r0 += kBatch) {
+        int segb[NS], segn[NS];   // segment start and padded length (a multiple of 4)
+        bool ready = false;
+        if (rmode == kRecRead && rp + 16 <= rend) {
+            // the batch as the record pass left it: header, then its t and offsets
+            const int4 hd = __ldg(reinterpret_cast<const int4 *>(rp));
+            const int R = rec_unpack(hd, segb, segn);
+            const bool slow = (hd.w >> 16) != 0;
+            if (!slow) {
+                const float4 *gt = reinterpret_cast<const float4 *>(rp + 16);
+                const int4 *gp = reinterpret_cast<const int4 *>(rp + 16 + 4 * R);
+                for (int i = lane; i < R / 4; i += 32) {
+                    reinterpret_cast<float4 *>(ent_t)[i] = __ldg(gt + i);
+                    reinterpret_cast<int4 *>(ent_p)[i] = __ldg(gp + i);
+                }
+                __syncwarp();
+                ready = true;
+            }
+            rp += 16 + 8 * (slow ? 0 : R);   // a flagged batch was stored without records
+        }
+        if (!ready) {
         // ---- A: lane per row
         float tv[kRowsPerLane];
         int pv[kRowsPerLane], sv[kRowsPerLane];
         unsigned long long own = 0ull;
+        const float fr0 = (float)(r0 + lane - H.r_ref);   // row offsets as exact floats
 #pragma unroll
         for (int j = 0; j < kRowsPerLane; ++j) {
             const int r = r0 + j * 32 + lane;
@@ -282,7 +346,18 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
             tv[j] = 0.f;
             pv[j] = 0;
             if (r < re) {
-                const RowEval e = row_eval<DEG>(H, s, inv_a, sgn, r);
+                RowEval e;
+                if constexpr (DEG == 0) {
+                    e = row_eval<0>(H, s, inv_a, sgn, r);
+                } else {
+                    // as row_eval, with one float-to-int conversion per row
+                    int k;
+                    const float u0 = row_start_f(H, inv_a, fr0 + (float)(32 * j), k);
+                    float s_lo;
+                    e.sg = sigma_of<DEG>(s, u0, s_lo);
+                    e.t = u0 - s_lo;
+                    e.q0 = H.q_ref - sgn * k;
+                }
                 const int rr = r - S0;
                 const int oq = e.q0 - clo[rr];
                 const int lo = sgn > 0 ? oq : oq - (K - 1);
@@ -292,6 +367,9 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
                     tv[j] = e.t;
                     pv[j] = rr * kPitch + oq;
                     own += 1ull << (9 * e.sg);
+                } else if (rmode == kRecWrite) {
+                    // the replay recomputes this batch (and reaches global memory then)
+                    own |= kRecSlowBit;
                 } else {
                     // run outside the staged window: straight from or to global memory
                     atomicAdd(err, 1);
@@ -310,6 +388,8 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
             }
         }
         // counting sort by sigma: 9-bit counters per interval, packed
+        const bool slow_batch = rmode == kRecWrite && __any_sync(0xffffffffu, (own & kRecSlowBit) != 0ull);
+        own &= ~kRecSlowBit;
         unsigned long long inc = own;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -317,7 +397,6 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
             if (lane >= o) inc += y;
         }
         const unsigned long long tot = __shfl_sync(0xffffffffu, inc, 31);
-        int segb[NS], segn[NS];   // segment start and padded length (a multiple of 4)
         unsigned long long basep = 0ull;
         {
             int b = 0;
@@ -345,6 +424,29 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
             }
         }
         __syncwarp();
+        if (rmode == kRecWrite) {
+            // store the batch for the replays: header, t[R], offsets[R] (a
+            // batch that would not fit the line's region is stored flagged,
+            // without records; past its end nothing is stored, and the
+            // replay, reading the same positions, recomputes those batches)
+            if (rp + 16 > rend) continue;
+            int R = 0;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) R += segn[q];
+            const bool flag = slow_batch || rp + 16 + 8 * R > rend;
+            if (flag) R = 0;
+            if (lane == 0) *reinterpret_cast<int4 *>(rp) = rec_pack(segn, flag);
+            float4 *gt = reinterpret_cast<float4 *>(rp + 16);
+            int4 *gp = reinterpret_cast<int4 *>(rp + 16 + 4 * R);
+            for (int i = lane; i < R / 4; i += 32) {
+                gt[i] = reinterpret_cast<const float4 *>(ent_t)[i];
+                gp[i] = reinterpret_cast<const int4 *>(ent_p)[i];
+            }
+            rp += 16 + 8 * R;
+            __syncwarp();
+            continue;
+        }
+        }   // !ready
         // ---- B: lane per (candidate, row slot), four rows per step
         if (lane_on) {
             f2 C[NC];
@@ -403,14 +505,15 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
 // transposed image).
 // One chunk (view v, bins j0..j0+31) of one instance; smem is the CTA's
 // dynamic shared memory (kSmemBytes).
-template <int DEG, bool ADJ, bool CONCAT = ADJ>
+template <int DEG, bool ADJ, bool CONCAT = ADJ, int RM = kRecNone>
 __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g, const LinesDev L,
                                             const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
                                             const float *__restrict__ coef, const float *__restrict__ coefT,
                                             float *__restrict__ sino, float *__restrict__ out,
                                             float *__restrict__ outT, int chunks_per_view, int vec, int *err,
-                                            int chunk)
+                                            int chunk, unsigned char *rec = nullptr, long long rec_cap = 0)
 {
+    constexpr int rmode = RM;
     float *strip = reinterpret_cast<float *>(smem);
     size_t o = kStripBytes;
     int *clo = reinterpret_cast<int *>(smem + o);
@@ -423,6 +526,8 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
     o += kMiscBytes;
     int *gstack = misc + 8;   // pending line groups, (first | last << 8)
     LineHdr *hdr_s = reinterpret_cast<LineHdr *>(smem + o);
+    o += kHdrBytes;
+    int *rec_off = reinterpret_cast<int *>(smem + o);   // per line: bytes of its records used so far
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *tabbuf = reinterpret_cast<float *>(warp_area + warp * kWarpBytes);   // [2][kTabFloats]
@@ -434,6 +539,7 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
     const int64_t line0 = (int64_t)v * L.n_det + j0;
 
     if (!ADJ && threadIdx.x < kChunk) line_acc[threadIdx.x] = 0.f;
+    if (threadIdx.x < kChunk) rec_off[threadIdx.x] = 0;
     if (!ADJ && threadIdx.x < kDummy) strip[kSlabRows * kPitch + threadIdx.x] = 0.f;
     // the chunk's line records into shared memory, its tables towards L2
     for (int i = threadIdx.x; i < nl * 4; i += kThreads)
@@ -482,7 +588,9 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
             if (lane < nl) {
                 const LineHdr &H = hdr_s[lane];
                 mine = !(H.flags & kEmpty) && (((H.flags & kVert) != 0) == (axis == 0)) && H.r_end > H.r_begin;
-                if (ADJ && mine) mine = sino[line0 + lane] != 0.f;
+                // (with kept records the groups must be those of the record pass,
+                // so lines with p = 0 stay in them and are skipped below)
+                if (ADJ && mine && rmode == kRecNone) mine = sino[line0 + lane] != 0.f;
             }
             const unsigned mask = __ballot_sync(0xffffffffu, mine);
             if (lane == 0) {
@@ -560,7 +668,9 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                 }
                 __syncthreads();
                 constexpr int kCh = kPitch / 4;   // 16-byte chunks per strip row
-                if constexpr (ADJ) {
+                if (rmode == kRecWrite) {
+                    // the record pass projects nothing: no strip
+                } else if constexpr (ADJ) {
                     float4 *s4 = reinterpret_cast<float4 *>(strip);
                     for (int i = threadIdx.x; i < nrows * kCh; i += kThreads) s4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
                 } else if (vec) {
@@ -592,43 +702,67 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                     asm volatile("cp.async.wait_all;" ::: "memory");
                 }
                 __syncthreads();
-                // this warp's lines of the group: li = first + warp + k kWarps in gmask;
-                // the table of the next one is loaded while the current one runs
+                // this warp's lines of the group: li = first + warp + k kWarps in
+                // wmask (gmask less, in the adjoint with kept records, lines with
+                // p = 0); the table of the next one is loaded while the current
+                // one runs.  The record pass needs only each table's head (the
+                // interval ends s_q); replays prefetch a line's records one line
+                // ahead.
+                unsigned wmask = gmask;
+                if (ADJ && rmode == kRecRead) {
+                    const bool nz = lane < nl && sino[line0 + lane] != 0.f;
+                    wmask &= __ballot_sync(0xffffffffu, nz);
+                }
                 int li = first + warp;
-                while (li <= last && !((gmask >> li) & 1u)) li += kWarps;
+                while (li <= last && !((wmask >> li) & 1u)) li += kWarps;
                 int buf = 0;
+                const int tab16 = rmode == kRecWrite ? kTabHead / 4 : kTabFloats / 4;
+                constexpr int kRecAhead = 4096;
                 if (li <= last) {
-                    table_copy_async(tabbuf, tabs + (int64_t)hdr_s[li].tab * kTabFloats, lane);
+                    table_copy_async(tabbuf, tabs + (int64_t)hdr_s[li].tab * kTabFloats, lane, tab16);
                     cp_async_commit();
+                    if (rmode == kRecRead)
+                        prefetch_span_l2(rec + (line0 + li) * rec_cap + rec_off[li],
+                                         (int)min((long long)kRecAhead, rec_cap - rec_off[li]), lane);
                 }
                 while (li <= last) {
                     int ln = li + kWarps;
-                    while (ln <= last && !((gmask >> ln) & 1u)) ln += kWarps;
-                    if (ln <= last)
+                    while (ln <= last && !((wmask >> ln) & 1u)) ln += kWarps;
+                    if (ln <= last) {
                         table_copy_async(tabbuf + (buf ^ 1) * kTabFloats,
-                                         tabs + (int64_t)hdr_s[ln].tab * kTabFloats, lane);
+                                         tabs + (int64_t)hdr_s[ln].tab * kTabFloats, lane, tab16);
+                        if (rmode == kRecRead)
+                            prefetch_span_l2(rec + (line0 + ln) * rec_cap + rec_off[ln],
+                                             (int)min((long long)kRecAhead, rec_cap - rec_off[ln]), lane);
+                    }
                     cp_async_commit();
                     cp_async_wait<1>();
                     __syncwarp();
                     const LineHdr H = hdr_s[li];
                     const float hp = ADJ ? g.h * sino[line0 + li] : 0.f;
+                    unsigned char *lrec = rec ? rec + (line0 + li) * rec_cap : nullptr;
+                    unsigned char *rp = lrec ? lrec + rec_off[li] : nullptr;
+                    const unsigned char *rend = lrec ? lrec + rec_cap : nullptr;
                     float part;
                     if (ADJ && fixed)
-                        part = strip_line<DEG, ADJ, CONCAT, true>(H, tabbuf + buf * kTabFloats, ent_t, ent_p, strip, clo,
-                                                                  S0, S1, lane, src, dst, Nq, err, hp, hp * fscale);
+                        part = strip_line<DEG, ADJ, CONCAT, true, RM>(H, tabbuf + buf * kTabFloats, ent_t, ent_p, strip,
+                                                                      clo, S0, S1, lane, src, dst, Nq, err, hp,
+                                                                      hp * fscale, rp, rend);
                     else
-                        part = strip_line<DEG, ADJ, CONCAT, false>(H, tabbuf + buf * kTabFloats, ent_t, ent_p, strip,
-                                                                   clo, S0, S1, lane, src, dst, Nq, err, hp, 0.f);
-                    if (!ADJ) {
+                        part = strip_line<DEG, ADJ, CONCAT, false, RM>(H, tabbuf + buf * kTabFloats, ent_t, ent_p,
+                                                                       strip, clo, S0, S1, lane, src, dst, Nq, err, hp,
+                                                                       0.f, rp, rend);
+                    if (!ADJ && rmode != kRecWrite) {
                         const float sum = warp_sum(part);
                         if (lane == 0) line_acc[li] += sum;
                     }
+                    if (lrec && lane == 0) rec_off[li] = (int)(rp - lrec);
                     __syncwarp();
                     li = ln;
                     buf ^= 1;
                 }
                 cp_async_wait<0>();
-                if constexpr (ADJ) {
+                if (ADJ && rmode != kRecWrite) {
                     __syncthreads();
                     // add the accumulated strip into the image
                     if (vec) {
@@ -665,21 +799,22 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
             }
         }
     }
-    if constexpr (!ADJ) {
+    if (!ADJ && rmode != kRecWrite) {
         __syncthreads();
         if (threadIdx.x < nl) sino[line0 + threadIdx.x] = g.h * line_acc[threadIdx.x];
     }
 }
 
-template <int DEG, bool ADJ>
+template <int DEG, bool ADJ, int RM>
 __global__ void __launch_bounds__(kThreads, 2)
 strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
              const float *__restrict__ coef, const float *__restrict__ coefT, float *__restrict__ sino,
-             float *__restrict__ out, float *__restrict__ outT, int chunks_per_view, int vec, int *err)
+             float *__restrict__ out, float *__restrict__ outT, int chunks_per_view, int vec, int *err,
+             unsigned char *rec, long long rec_cap)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    strip_chunk<DEG, ADJ>(smem, g, L, hdr, tabs, coef, coefT, sino, out, outT, chunks_per_view, vec, err,
-                          (int)blockIdx.x);
+    strip_chunk<DEG, ADJ, ADJ, RM>(smem, g, L, hdr, tabs, coef, coefT, sino, out, outT, chunks_per_view, vec, err,
+                                   (int)blockIdx.x, rec, rec_cap);
 }
 
 // Persistent kernel over the chunks of several instances: each CTA takes the
@@ -756,18 +891,27 @@ __global__ void add_transposed_kernel(const float *__restrict__ inT, float *__re
 
 template <int DEG, bool ADJ>
 cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
-                           const float *coef, float *imgT, float *sino, float *out, int *err, cudaStream_t s)
+                           const float *coef, float *imgT, float *sino, float *out, int *err, cudaStream_t s,
+                           const StripRec *rec = nullptr, int rmode = kRecNone)
 {
     const dim3 tb(32, 8), tg((g.nx + 31) / 32, (g.ny + 31) / 32);
     cudaError_t e;
-    if (!ADJ) {
+    unsigned char *rb = (rec && rmode != kRecNone) ? rec->base : nullptr;
+    const long long rcap = rb ? rec->line_bytes : 0;
+    if (!rb) rmode = kRecNone;
+    if (rmode == kRecWrite) {
+        // records only: no image in or out
+    } else if (!ADJ) {
         transpose_kernel<<<tg, tb, 0, s>>>(coef, imgT, g.nx, g.ny);
     } else {
         e = cudaMemsetAsync(out, 0, sizeof(float) * (size_t)g.nx * g.ny, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(imgT, 0, sizeof(float) * (size_t)g.nx * g.ny, s);
         if (e != cudaSuccess) return e;
     }
-    e = cudaFuncSetAttribute(strip_kernel<DEG, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    auto kern = rmode == kRecRead ? strip_kernel<DEG, ADJ, kRecRead>
+                : rmode == kRecWrite ? strip_kernel<DEG, ADJ, (ADJ ? kRecNone : kRecWrite)>
+                                     : strip_kernel<DEG, ADJ, kRecNone>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     const int cpv = (L.n_det + kChunk - 1) / kChunk;
     const unsigned grid = (unsigned)(L.n_view * cpv);
@@ -775,10 +919,10 @@ cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *h
     const float *img = ADJ ? out : coef;
     const int vec = (g.nx % 4 == 0) && (g.ny % 4 == 0) && ((reinterpret_cast<uintptr_t>(img) & 15) == 0) &&
                     ((reinterpret_cast<uintptr_t>(imgT) & 15) == 0);
-    strip_kernel<DEG, ADJ><<<grid, kThreads, kSmemBytes, s>>>(g, L, hdr, tabs, coef, imgT,
-                                                              const_cast<float *>(sino), out, imgT, cpv, vec, err);
+    kern<<<grid, kThreads, kSmemBytes, s>>>(g, L, hdr, tabs, coef, imgT, const_cast<float *>(sino), out, imgT, cpv,
+                                            vec, err, rb, rcap);
     e = cudaGetLastError();
-    if (e == cudaSuccess && ADJ) {
+    if (e == cudaSuccess && ADJ && rmode != kRecWrite) {
         add_transposed_kernel<<<tg, tb, 0, s>>>(imgT, out, g.nx, g.ny);
         e = cudaGetLastError();
     }
@@ -861,28 +1005,56 @@ bool strip_supported(const GridDev &g, const LinesDev &L)
 
 size_t strip_scratch_bytes(const GridDev &g) { return sizeof(float) * (size_t)g.nx * g.ny + 256; }
 
+long long strip_rec_line_bytes(const GridDev &g)
+{
+    // A line's rows lie in [0, Nr) (Nr the grid's extent along its major
+    // axis) and are split into strip slabs of kSlabRows, each into batches of
+    // kBatch: at most nb = 2 ceil(Nr / kSlabRows) batches, hence at most
+    // Nr + nb 3 (n + 2) records (each interval segment padded by at most 3),
+    // 8 bytes each, and a 16-byte header per batch.
+    const long long nr = g.nx > g.ny ? g.nx : g.ny;
+    const long long nb = 2 * ((nr + kSlabRows - 1) / kSlabRows) + 2;
+    const long long bytes = nb * 16 + 8 * (nr + nb * 3 * (g.kdeg + 2));
+    return (bytes + 15) & ~15LL;
+}
+
 cudaError_t launch_fwd_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
-                             const float *coef, void *scratch, float *sino, int *err, cudaStream_t s)
+                             const float *coef, void *scratch, float *sino, int *err, cudaStream_t s,
+                             const StripRec *rec)
 {
     float *coefT = static_cast<float *>(scratch);
+    const int rm = rec ? kRecRead : kRecNone;
     switch (g.kdeg) {
-    case 0: return launch_strip_t<0, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
-    case 1: return launch_strip_t<1, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
-    case 2: return launch_strip_t<2, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
-    default: return launch_strip_t<3, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s);
+    case 0: return launch_strip_t<0, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s, rec, rm);
+    case 1: return launch_strip_t<1, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s, rec, rm);
+    case 2: return launch_strip_t<2, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s, rec, rm);
+    default: return launch_strip_t<3, false>(g, L, hdr, tabs, coef, coefT, sino, nullptr, err, s, rec, rm);
     }
 }
 
 cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
-                             const float *sino, void *scratch, float *coef_out, int *err, cudaStream_t s)
+                             const float *sino, void *scratch, float *coef_out, int *err, cudaStream_t s,
+                             const StripRec *rec)
 {
     float *outT = static_cast<float *>(scratch);
     float *p = const_cast<float *>(sino);
+    const int rm = rec ? kRecRead : kRecNone;
     switch (g.kdeg) {
-    case 0: return launch_strip_t<0, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);
-    case 1: return launch_strip_t<1, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);
-    case 2: return launch_strip_t<2, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);
-    default: return launch_strip_t<3, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s);
+    case 0: return launch_strip_t<0, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm);
+    case 1: return launch_strip_t<1, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm);
+    case 2: return launch_strip_t<2, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm);
+    default: return launch_strip_t<3, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm);
+    }
+}
+
+cudaError_t launch_strip_record(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
+                                const StripRec &rec, cudaStream_t s)
+{
+    switch (g.kdeg) {
+    case 0: return launch_strip_t<0, false>(g, L, hdr, tabs, nullptr, nullptr, nullptr, nullptr, nullptr, s, &rec, kRecWrite);
+    case 1: return launch_strip_t<1, false>(g, L, hdr, tabs, nullptr, nullptr, nullptr, nullptr, nullptr, s, &rec, kRecWrite);
+    case 2: return launch_strip_t<2, false>(g, L, hdr, tabs, nullptr, nullptr, nullptr, nullptr, nullptr, s, &rec, kRecWrite);
+    default: return launch_strip_t<3, false>(g, L, hdr, tabs, nullptr, nullptr, nullptr, nullptr, nullptr, s, &rec, kRecWrite);
     }
 }
 
