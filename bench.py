@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cg", action="store_true", help="skip the CGLS timing (not part of the step)")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch timing (not part of the step)")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start timing (not part of the step)")
+    ap.add_argument("--no-schemes", action="store_true", help="skip timing the adjoint schemes (not part of the step)")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="size scale of the uneven batch")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="fan512_cubic (the benchmark) or fan256_cubic (small profiling case)")
@@ -489,6 +490,27 @@ def run_ours(args, rank, ws, local):
     h2d = coef_h.numel() * 4 + view_h.numel() * 4
     d2h = sino_h.numel() * 4 + back_h.numel() * 4
 
+    # Adjoint schemes timed on this workload and on the 256^2 cubic parallel
+    # beam (per-view tables): strip scatter, warp-per-line scatter, pixel-driven
+    # gather (spline_plan_autotune's measurements)
+    schemes = {}
+    if not args.no_schemes:
+        for name in (wl.name, "parallel256_cubic"):
+            w2 = wl if name == wl.name else workloads.workload(name)
+            g2 = w2.geometry
+            if g2.kind == "fan":
+                l2 = sp.Lines.fan(torch.from_numpy(g2.view_angle).to(dev), g2.dso, g2.dod, g2.n_det, g2.det0, g2.ddet)
+            else:
+                l2 = sp.Lines.parallel(torch.from_numpy(g2.view_angle).to(dev), g2.n_det, g2.det0, g2.ddet)
+            p2 = sp.Plan(sp.Grid(w2.n, w2.n, w2.degree, w2.h), l2, prepare=True)
+            c2 = torch.from_numpy(w2.coef).to(dev)
+            s2 = p2.fwd(c2)
+            _, a_path, ms = p2.autotune(c2, s2)
+            schemes[name] = {"adj_strip_scatter_ms": ms[2], "adj_warp_scatter_ms": ms[3], "adj_gather_ms": ms[4],
+                             "fwd_strip_ms": ms[0], "fwd_warp_ms": ms[1],
+                             "adj_choice": {1: "strip scatter", 2: "warp scatter", 3: "gather"}.get(a_path)}
+            p2.close()
+
     # The same step with row records kept by the plan (written by prepare,
     # read by both projections), as iterative solvers use it.
     rec = None
@@ -595,6 +617,8 @@ def run_ours(args, rank, ws, local):
         "clocks": clocks,
         "wall_s": wall,
     }
+    if schemes:
+        line["adjoint_schemes"] = schemes
     if rec is not None:
         line["with_row_records"] = rec
     if cg is not None:

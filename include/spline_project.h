@@ -218,18 +218,24 @@ sp_status spline_plan_cgls(sp_plan *plan, const float *b, float *x, int32_t iter
                            double *gamma_hist, void *stream);
 /*
  * Kernel choice of a plan, per direction: 0 = automatic (the strip kernels
- * for PARALLEL and FAN lines of degree >= 1, else the general kernels), 1 = strip kernels where they apply, 2 = general kernels
- * (warp per line).  Both give the same results within rounding (no paper
- * counterpart: this is an implementation choice).
+ * for PARALLEL and FAN lines of degree >= 1, else the general kernels),
+ * 1 = strip kernels where they apply (ray-driven: the adjoint scatters into
+ * shared-memory strips), 2 = general kernels (warp per line; the adjoint
+ * scatters with global atomics), and for the adjoint only 3 = pixel-driven
+ * gather (thread per node over every view, no atomics; PARALLEL and FAN
+ * lines of degree >= 1, else as 0).  All give the same results within
+ * rounding (no paper counterpart: this is an implementation choice).
  */
 sp_status spline_plan_set_paths(sp_plan *plan, int32_t fwd_path, int32_t adj_path);
 /*
- * Autotuner: times the forward and the adjoint with both kernel families on
- * the caller's data (coef: device [ny][nx], sino: device [m]; neither is
- * modified; outputs go to temporary buffers) and keeps the faster per
+ * Autotuner: times the forward with both kernel families and the adjoint
+ * with all three (strip scatter, warp-per-line scatter, pixel-driven gather)
+ * on the caller's data (coef: device [ny][nx], sino: device [m]; neither is
+ * modified; outputs go to temporary buffers) and keeps the fastest per
  * direction (spline_plan_set_paths).  Writes the choices to *fwd_path and
- * *adj_path and, if ms != NULL, the mean times ms[0..3] = forward strip,
- * forward general, adjoint strip, adjoint general (0 when not measured).
+ * *adj_path and, if ms != NULL, the mean times ms[0..4] = forward strip,
+ * forward general, adjoint strip, adjoint general, adjoint gather (0 when
+ * not measured).
  * Synchronises the stream; allocates and frees m + ny*nx floats.
  */
 sp_status spline_plan_autotune(sp_plan *plan, const float *coef, const float *sino, void *stream,

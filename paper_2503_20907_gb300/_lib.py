@@ -354,16 +354,17 @@ class Plan:
         return x, gam
 
     def set_paths(self, fwd: int, adj: int):
-        """Kernel family per direction: 0 automatic, 1 strip, 2 general."""
+        """Kernel family per direction: 0 automatic, 1 strip, 2 general; the
+        adjoint also 3, the pixel-driven gather."""
         _check(load().spline_plan_set_paths(self._h, int(fwd), int(adj)))
 
     def autotune(self, coef: torch.Tensor, sino: torch.Tensor, stream=None):
-        """Time both kernel families on this data and keep the faster per
+        """Time the kernel families on this data and keep the fastest per
         direction.  Returns (fwd_path, adj_path, [ms fwd strip, fwd general,
-        adj strip, adj general])."""
+        adj strip, adj general, adj gather])."""
         c, p = _dev_f32(coef, "coef"), _dev_f32(sino, "sino")
         f, a = ctypes.c_int32(0), ctypes.c_int32(0)
-        ms = (ctypes.c_float * 4)()
+        ms = (ctypes.c_float * 5)()
         _check(load().spline_plan_autotune(self._h, c.data_ptr(), p.data_ptr(), _stream(stream),
                                            ctypes.byref(f), ctypes.byref(a), ms))
         return f.value, a.value, list(ms)

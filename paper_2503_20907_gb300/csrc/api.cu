@@ -155,7 +155,8 @@ int *slow_counter(const spx::GridDev &g, void *extra)
 // general warp-per-line kernels.  kPathAuto takes the strip kernels for degree
 // >= 1 (at degree 0 a row has at most two candidates, too few to repay the
 // row records and their sort; the strip kernels run it when asked).
-enum KernelPath { kPathAuto = 0, kPathStrip = 1, kPathGeneral = 2 };
+// kPathGather (adjoint only): the pixel-driven gather where it applies.
+enum KernelPath { kPathAuto = 0, kPathStrip = 1, kPathGeneral = 2, kPathGather = 3 };
 
 bool use_strip(const spx::GridDev &g, const spx::LinesDev &L, void *extra, int path)
 {
@@ -177,6 +178,8 @@ cudaError_t run_adj(const spx::GridDev &g, const spx::LinesDev &L, const spx::Li
                     void *extra, const float *sino, float *coef_out, cudaStream_t s, int path = kPathAuto,
                     const spx::StripRec *rec = nullptr)
 {
+    if (path == kPathGather && spx::gather_supported(g, L))
+        return spx::launch_adj_gather(g, L, hdr, tabs, sino, coef_out, s);
     if (use_strip(g, L, extra, path))
         return spx::launch_adj_strip(g, L, hdr, tabs, sino, extra, coef_out, slow_counter(g, extra), s, rec);
     return spx::launch_adj(g, hdr, tabs, L.m, sino, coef_out, s);
@@ -570,7 +573,8 @@ sp_status spline_plan_set_paths(sp_plan *plan, int32_t fwd_path, int32_t adj_pat
 {
     g_err.clear();
     if (!plan) return fail(SP_EINVAL, "plan is NULL");
-    if (fwd_path < 0 || fwd_path > 2 || adj_path < 0 || adj_path > 2) return fail(SP_EINVAL, "path must be 0, 1 or 2");
+    if (fwd_path < 0 || fwd_path > 2 || adj_path < 0 || adj_path > 3)
+        return fail(SP_EINVAL, "path must be 0, 1 or 2 (the adjoint also 3)");
     plan->path_fwd = fwd_path;
     plan->path_adj = adj_path;
     return SP_OK;
@@ -586,19 +590,24 @@ sp_status spline_plan_autotune(sp_plan *plan, const float *coef, const float *si
     if (m > 0 && (!coef || !sino)) return fail(SP_EINVAL, "coef/sino pointers are NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool both = plan->extra && spx::strip_supported(plan->g, plan->L) && m > 0;
-    float t[4] = {0.f, 0.f, 0.f, 0.f};   // fwd strip, fwd general, adj strip, adj general
+    // fwd strip, fwd general, adj strip, adj general, adj gather
+    float t[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     int bf = both ? kPathStrip : kPathGeneral, ba = bf;
+    const bool gather = both && spx::gather_supported(plan->g, plan->L);
     if (both) {
         float *tmp_s = nullptr, *tmp_c = nullptr;
         cudaError_t e = cudaMalloc(&tmp_s, sizeof(float) * (size_t)m);
         if (e == cudaSuccess) e = cudaMalloc(&tmp_c, sizeof(float) * (size_t)n);
-        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
-            const int path = (k & 1) ? kPathGeneral : kPathStrip;
+        const spx::StripRec *rec = plan_rec(plan);
+        for (int k = 0; k < (gather ? 5 : 4) && e == cudaSuccess; ++k) {
+            const int path = k == 4 ? kPathGather : ((k & 1) ? kPathGeneral : kPathStrip);
             if (k < 2)
-                e = time_runs([&] { return run_fwd(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, coef, tmp_s, s, path); },
+                e = time_runs([&] { return run_fwd(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, coef, tmp_s, s,
+                                                   path, rec); },
                               3, s, &t[k]);
             else
-                e = time_runs([&] { return run_adj(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, sino, tmp_c, s, path); },
+                e = time_runs([&] { return run_adj(plan->g, plan->L, plan->hdr, plan->tabs, plan->extra, sino, tmp_c, s,
+                                                   path, rec); },
                               3, s, &t[k]);
         }
         cudaError_t e2 = cudaStreamSynchronize(s);
@@ -608,12 +617,13 @@ sp_status spline_plan_autotune(sp_plan *plan, const float *coef, const float *si
         if (e != cudaSuccess) return cuda_fail(e, "autotune");
         bf = t[0] <= t[1] ? kPathStrip : kPathGeneral;
         ba = t[2] <= t[3] ? kPathStrip : kPathGeneral;
+        if (gather && t[4] < (ba == kPathStrip ? t[2] : t[3])) ba = kPathGather;
     }
     plan->path_fwd = bf;
     plan->path_adj = ba;
     if (fwd_path) *fwd_path = bf;
     if (adj_path) *adj_path = ba;
-    if (ms_out) for (int k = 0; k < 4; ++k) ms_out[k] = t[k];
+    if (ms_out) for (int k = 0; k < 5; ++k) ms_out[k] = t[k];
     return SP_OK;
 }
 

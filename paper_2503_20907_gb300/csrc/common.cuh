@@ -293,6 +293,11 @@ cudaError_t launch_fwd_strip(const GridDev &g, const LinesDev &L, const LineHdr 
 cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
                              const float *sino, void *scratch, float *coef_out, int *slow_rows, cudaStream_t s,
                              const StripRec *rec = nullptr);
+// Pixel-driven adjoint (gather.cu): thread per node over all views, no
+// atomics; parallel and fan beams of degree >= 1.  coef_out is overwritten.
+bool gather_supported(const GridDev &g, const LinesDev &L);
+cudaError_t launch_adj_gather(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
+                              const float *sino, float *coef_out, cudaStream_t s);
 // The row records of every line of (g, L) into rec (after line setup and tables).
 cudaError_t launch_strip_record(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
                                 const StripRec &rec, cudaStream_t s);
