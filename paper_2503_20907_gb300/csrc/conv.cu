@@ -10,9 +10,15 @@
 //     staged in shared memory with padded strides (no bank conflicts on the
 //     fragment loads).  Epilogue: bias, optional ReLU, BF16 store.
 //   forward, 1 -> 32 and 32 -> 1: CUDA cores, thread per pixel.
-//   gradients (training): CUDA cores in FP32 with BF16 activations and
-//     weights read as stored; the input gradient can be gated by the ReLU of
-//     the layer below (x > 0).
+//   gradients of the 32 -> 32 layers (training), on the tensor cores too:
+//     the input gradient is the same kernel run on the incoming gradient g
+//     (rounded to BF16 while it is staged) with the weights flipped while
+//     they are staged (W'[i, 8 - tap, o] = W[o, tap, i]), FP32 output gated
+//     by the ReLU of the layer below; the weight gradient is a GEMM over the
+//     pixels (M = 32 output channels, N = 9 taps x 32 input channels, K =
+//     pixels) with g and x staged transposed, one partial sum per block
+//     added to the result.
+//   gradients of the 1 -> 32 and 32 -> 1 layers: CUDA cores in FP32.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -43,9 +49,14 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
 }
 
 // y = conv(x) + bias (ReLU optional), 32 -> 32 channels, taps dil apart.
-__global__ void __launch_bounds__(128) conv32_fwd_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
-                                                         const float *__restrict__ bias, bf16 *__restrict__ y,
-                                                         int B, int H, int W, int relu, int dil)
+// GRAD: the input gradient instead: x is the FP32 gradient g of the layer's
+// output (rounded to BF16 here), w the layer's weights (flipped here), y the
+// FP32 gradient of its input, zeroed where gate <= 0 (gate may be NULL).
+template <bool GRAD>
+__global__ void __launch_bounds__(128) conv32_fwd_kernel(const void *__restrict__ xv, const bf16 *__restrict__ w,
+                                                         const float *__restrict__ bias, void *__restrict__ yv,
+                                                         int B, int H, int W, int relu, int dil,
+                                                         const bf16 *__restrict__ gate)
 {
     __shared__ __align__(16) bf16 xs[3][kTileW + 2 * kMaxDil][kXStride];
     __shared__ __align__(16) bf16 ws[kC][kWStride];
@@ -54,10 +65,22 @@ __global__ void __launch_bounds__(128) conv32_fwd_kernel(const bf16 *__restrict_
     const int h = (blockIdx.x / tiles_w) % H;
     const int b = blockIdx.x / (tiles_w * H);
     const int w0 = tw * kTileW;
-    // weights: 32 x 288 bf16, 16-byte chunks (36 per channel)
-    for (int i = threadIdx.x; i < kC * 36; i += 128) {
-        const int o = i / 36, c = i - o * 36;
-        *reinterpret_cast<uint4 *>(&ws[o][c * 8]) = *reinterpret_cast<const uint4 *>(w + (size_t)o * 9 * kC + c * 8);
+    if constexpr (!GRAD) {
+        // weights: 32 x 288 bf16, 16-byte chunks (36 per channel)
+        for (int i = threadIdx.x; i < kC * 36; i += 128) {
+            const int o = i / 36, c = i - o * 36;
+            *reinterpret_cast<uint4 *>(&ws[o][c * 8]) =
+                *reinterpret_cast<const uint4 *>(w + (size_t)o * 9 * kC + c * 8);
+        }
+    } else {
+        // flipped: ws[i][(8 - tap) 32 + o] = W[o][tap][i], read in 16-byte chunks of 8 i
+        for (int j = threadIdx.x; j < kC * 36; j += 128) {
+            const int o = j / 36, rem = j - o * 36, tap = rem >> 2, i0 = (rem & 3) * 8;
+            const uint4 v = *reinterpret_cast<const uint4 *>(w + ((size_t)o * 9 + tap) * kC + i0);
+            const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ws[i0 + k][(8 - tap) * kC + o] = e[k];
+        }
     }
     // input rows h-dil, h, h+dil, pixels w0-dil..w0+63+dil, 16-byte chunks of 8 channels
     const int tw2 = kTileW + 2 * dil;
@@ -66,8 +89,18 @@ __global__ void __launch_bounds__(128) conv32_fwd_kernel(const bf16 *__restrict_
         const int p = rem >> 2, c = rem & 3;
         const int hh = h + (r - 1) * dil, ww = w0 + p - dil;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (hh >= 0 && hh < H && ww >= 0 && ww < W)
-            v = *reinterpret_cast<const uint4 *>(x + (((size_t)b * H + hh) * W + ww) * kC + c * 8);
+        if (hh >= 0 && hh < H && ww >= 0 && ww < W) {
+            const size_t off = (((size_t)b * H + hh) * W + ww) * kC + c * 8;
+            if constexpr (GRAD) {
+                const float4 f0 = *reinterpret_cast<const float4 *>(static_cast<const float *>(xv) + off);
+                const float4 f1 = *reinterpret_cast<const float4 *>(static_cast<const float *>(xv) + off + 4);
+                __nv_bfloat162 q[4] = {__floats2bfloat162_rn(f0.x, f0.y), __floats2bfloat162_rn(f0.z, f0.w),
+                                       __floats2bfloat162_rn(f1.x, f1.y), __floats2bfloat162_rn(f1.z, f1.w)};
+                v = *reinterpret_cast<const uint4 *>(q);
+            } else {
+                v = *reinterpret_cast<const uint4 *>(static_cast<const bf16 *>(xv) + off);
+            }
+        }
         *reinterpret_cast<uint4 *>(&xs[r][p][c * 8]) = v;
     }
     __syncthreads();
@@ -109,9 +142,17 @@ __global__ void __launch_bounds__(128) conv32_fwd_kernel(const bf16 *__restrict_
             const int ww = w0 + pb + g + 8 * half;
             if (ww >= W) continue;
             float v0 = acc[nt][2 * half] + b0, v1 = acc[nt][2 * half + 1] + b1;
-            if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
-            *reinterpret_cast<__nv_bfloat162 *>(y + (((size_t)b * H + h) * W + ww) * kC + o) =
-                __floats2bfloat162_rn(v0, v1);
+            const size_t off = (((size_t)b * H + h) * W + ww) * kC + o;
+            if constexpr (GRAD) {
+                if (gate) {
+                    if (!(__bfloat162float(gate[off]) > 0.f)) v0 = 0.f;
+                    if (!(__bfloat162float(gate[off + 1]) > 0.f)) v1 = 0.f;
+                }
+                *reinterpret_cast<float2 *>(static_cast<float *>(yv) + off) = make_float2(v0, v1);
+            } else {
+                if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(yv) + off) = __floats2bfloat162_rn(v0, v1);
+            }
         }
     }
 }
@@ -265,6 +306,101 @@ __global__ void conv_wgrad_kernel(const bf16 *__restrict__ x, const float *__res
     }
 }
 
+// Weight gradient of a 32 -> 32 layer on the tensor cores:
+//   dW[o, tap, i] += sum_p g[p, o] x[p + off(tap), i],  dbias[o] += sum_p g[p, o]
+// as a GEMM with M = o (two 16-row tiles), N = (tap, i) (36 tiles of 8), K =
+// pixels.  A block takes `rows` image rows (over B*H), each in chunks of
+// kWgPix pixels: the chunk of g, rounded to BF16, transposed to [o][p], and
+// for each of the nine taps the shifted chunk of x transposed to [i][p]
+// (zero outside the image), so that every fragment is a pair of consecutive
+// pixels.  Warp w owns N tiles 9w..9w+8 of both M tiles (72 accumulators
+// per thread); the block adds its partial sums to dw and dbias at the end.
+constexpr int kWgPix = 64;                // pixels per staged chunk
+constexpr int kWgStride = kWgPix + 8;     // bf16 per staged channel row (conflict-free fragment loads)
+
+__global__ void __launch_bounds__(128) conv32_wgrad_kernel(const bf16 *__restrict__ x, const float *__restrict__ g,
+                                                           float *__restrict__ dw, float *__restrict__ db, int B,
+                                                           int H, int W, int rows, int dil)
+{
+    __shared__ __align__(16) bf16 gs[kC][kWgStride];          // g^T of the chunk
+    __shared__ __align__(16) bf16 xs[9][kC][kWgStride];       // x^T shifted by each tap
+    __shared__ float bsum[kC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gq = lane >> 2, t = lane & 3;
+    float acc[2][9][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int n = 0; n < 9; ++n)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[mt][n][k] = 0.f;
+    if (threadIdx.x < kC) bsum[threadIdx.x] = 0.f;
+    float bpart = 0.f;   // dbias of channel (threadIdx.x & 31), partial
+    const int r0 = blockIdx.x * rows, r1 = min(r0 + rows, B * H);
+    for (int r = r0; r < r1; ++r) {
+        const int bb = r / H, hh = r - bb * H;
+        for (int c0 = 0; c0 < W; c0 += kWgPix) {
+            __syncthreads();
+            // g chunk: thread (channel o = tid & 31, pixel group) reads along pixels
+            for (int k = threadIdx.x; k < kC * kWgPix; k += 128) {
+                const int o = k & 31, pp = k >> 5;
+                const int ww = c0 + pp;
+                const float v = ww < W ? g[(((size_t)bb * H + hh) * W + ww) * kC + o] : 0.f;
+                gs[o][pp] = __float2bfloat16(v);
+                bpart += v;
+            }
+            // x chunks for the nine taps: xs[tap][i][pp] = x[hh + (ky-1)d, c0 + pp + (kx-1)d, i]
+            for (int k = threadIdx.x; k < 9 * kC * kWgPix; k += 128) {
+                const int i = k & 31, rem = k >> 5, pp = rem % kWgPix, tap = rem / kWgPix;
+                const int y0 = hh + (tap / 3 - 1) * dil, x0 = c0 + pp + (tap % 3 - 1) * dil;
+                xs[tap][i][pp] = (y0 >= 0 && y0 < H && x0 >= 0 && x0 < W)
+                                     ? x[(((size_t)bb * H + y0) * W + x0) * kC + i]
+                                     : __float2bfloat16(0.f);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kc = 0; kc < kWgPix; kc += 16) {
+                uint32_t a[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int m = mt * 16 + gq;
+                    a[mt][0] = *reinterpret_cast<const uint32_t *>(&gs[m][kc + 2 * t]);
+                    a[mt][1] = *reinterpret_cast<const uint32_t *>(&gs[m + 8][kc + 2 * t]);
+                    a[mt][2] = *reinterpret_cast<const uint32_t *>(&gs[m][kc + 2 * t + 8]);
+                    a[mt][3] = *reinterpret_cast<const uint32_t *>(&gs[m + 8][kc + 2 * t + 8]);
+                }
+#pragma unroll
+                for (int n = 0; n < 9; ++n) {
+                    const int nt = warp * 9 + n;           // N tile: tap nt / 4, channels 8 (nt % 4)..
+                    const int tap = nt >> 2, i = (nt & 3) * 8 + gq;
+                    const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&xs[tap][i][kc + 2 * t]);
+                    const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&xs[tap][i][kc + 2 * t + 8]);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+                        mma_bf16(acc[mt][n], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                }
+            }
+        }
+    }
+    // accumulator (mt, n): rows o = 16 mt + gq (+8), columns N = 8 nt + 2t (+1)
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int n = 0; n < 9; ++n) {
+            const int nt = warp * 9 + n, tap = nt >> 2, i = (nt & 3) * 8 + 2 * t;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int o = mt * 16 + gq + 8 * half;
+                float *d = dw + ((size_t)o * 9 + tap) * kC + i;
+                atomicAdd(d, acc[mt][n][2 * half]);
+                atomicAdd(d + 1, acc[mt][n][2 * half + 1]);
+            }
+        }
+    atomicAdd(&bsum[threadIdx.x & 31], bpart);
+    __syncthreads();
+    if (threadIdx.x < kC) atomicAdd(db + threadIdx.x, bsum[threadIdx.x]);
+}
+
 // W'[i, 2-ky, 2-kx, o] = W[o, ky, kx, i] (the input gradient as a forward convolution)
 __global__ void flip_weights_kernel(const bf16 *__restrict__ w, bf16 *__restrict__ wf, int cin, int cout)
 {
@@ -297,8 +433,8 @@ sp_status sp_conv3x3_fwd(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t c
         const int tiles = (W + spx::kTileW - 1) / spx::kTileW;
         const int64_t grid = (int64_t)B * H * tiles;
         if (grid > 0x7fffffff) return spx::record_error(SP_EINVAL, "too many tiles");
-        spx::conv32_fwd_kernel<<<(unsigned)grid, 128, 0, s>>>(xb, wb, bias, static_cast<spx::bf16 *>(y), B, H, W,
-                                                             relu, dilation);
+        spx::conv32_fwd_kernel<false><<<(unsigned)grid, 128, 0, s>>>(xb, wb, bias, y, B, H, W, relu, dilation,
+                                                                    nullptr);
     } else {
         const int64_t n = (int64_t)B * H * W;
         int64_t blocks = (n + 255) / 256;
@@ -324,9 +460,14 @@ sp_status sp_conv3x3_bwd_data(int32_t B, int32_t H, int32_t W, int32_t cin, int3
     if (blocks > 152 * 16) blocks = 152 * 16;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const spx::bf16 *wb = static_cast<const spx::bf16 *>(w), *gb = static_cast<const spx::bf16 *>(gate);
-    if (cin == 32 && cout == 32)
-        spx::conv_dgrad_kernel<32, 32><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W, dilation);
-    else if (cin == 32)
+    if (cin == 32 && cout == 32) {
+        if ((reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(dx)) & 15)
+            return spx::record_error(SP_EINVAL, "g, w, dx must be 16-byte aligned");
+        const int tiles = (W + spx::kTileW - 1) / spx::kTileW;
+        const int64_t grid = (int64_t)B * H * tiles;
+        if (grid > 0x7fffffff) return spx::record_error(SP_EINVAL, "too many tiles");
+        spx::conv32_fwd_kernel<true><<<(unsigned)grid, 128, 0, s>>>(g, wb, nullptr, dx, B, H, W, 0, dilation, gb);
+    } else if (cin == 32)
         spx::conv_dgrad_kernel<32, 1><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W, dilation);
     else
         spx::conv_dgrad_kernel<1, 32><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W, dilation);
@@ -346,6 +487,16 @@ sp_status sp_conv3x3_bwd_weight(int32_t B, int32_t H, int32_t W, int32_t cin, in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * (size_t)cout * 9 * cin, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dbias, 0, sizeof(float) * (size_t)cout, s);
+    if (cin == 32 && cout == 32) {
+        if (e == cudaSuccess) {
+            const int rows = 16;
+            const int blocks = (B * H + rows - 1) / rows;
+            spx::conv32_wgrad_kernel<<<blocks, 128, 0, s>>>(static_cast<const spx::bf16 *>(x), g, dw, dbias, B, H, W,
+                                                            rows, dilation);
+            e = cudaGetLastError();
+        }
+        return e == cudaSuccess ? SP_OK : spx::record_error(SP_ECUDA, cudaGetErrorString(e));
+    }
     const size_t sh = sizeof(float) * (size_t)W * cout + sizeof(spx::bf16) * 3 * (size_t)(W + 2 * dilation) * cin;
     if (sh > 200 * 1024) return spx::record_error(SP_EINVAL, "image too wide for the weight-gradient kernel");
     const int OB = cout < 4 ? cout : 4, IB = cin < 4 ? cin : 4;

@@ -95,9 +95,12 @@ __device__ __forceinline__ void red_shared(float *p, float v)
                  : "memory");
 }
 
+// No "memory" clobber: the strip is read only after the block's barrier
+// before its flush, so the reductions need not order the row-record and table
+// loads of the next groups, which the compiler may then issue early.
 __device__ __forceinline__ void red_shared_u32(int *p, int v)
 {
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v));
 }
 
 // Fixed-point rounding constant M = 1.5 * 2^23 (see the top of the file).

@@ -141,18 +141,45 @@ def make_samples(plan: Plan, seeds, device, alpha: float | None = None, peak: fl
 
 
 # ------------------------------------------------------------------ training
+def cgls_residual_after(plan: Plan, x0, b, iters: int):
+    """||A^T (b - A x_K)||^2 after K = iters CGLS steps from x0 (the CGLS
+    recurrences of spline_plan_cgls), differentiable in x0 through the
+    projector's autograd functions: A and A^T are linear, the step lengths
+    alpha and beta are differentiable functions of the iterates."""
+    from .autograd import backproject, project
+    r = b - project(x0, plan)
+    s = backproject(r, plan)
+    p = s
+    gamma = (s * s).sum()
+    for _ in range(iters):
+        q = project(p, plan)
+        alpha = gamma / (q * q).sum().clamp_min(1e-30)
+        r = r - alpha * q
+        s = backproject(r, plan)
+        gamma_new = (s * s).sum()
+        p = s + (gamma_new / gamma.clamp_min(1e-30)) * p
+        gamma = gamma_new
+    return gamma
+
+
 def train(n_train=20000, batch=16, epochs=1, lr=1e-3, device="cuda", log=print, chunk=500, target_iters=0,
-          loss_kind="residual"):
-    """loss_kind 'residual': mean over the batch of ||A^T (b - A x_0)||^2 / ||A^T b||^2,
-    the quantity CGLS is judged by, differentiated through the projector's
-    autograd functions; 'mse': ||x_0 - target||^2 against the phantom
-    (target_iters = 0) or a CGLS iterate."""
+          loss_kind="residual", cg_steps=0, init=None):
+    """loss_kind 'residual': mean over the batch of ||A^T (b - A x_K)||^2 / ||A^T b||^2
+    where x_K is CGLS after cg_steps iterations from x_0 = net(z) (cg_steps = 0:
+    x_0 itself), the quantity CGLS is judged by, differentiated through the
+    projector's autograd functions (the residual left after K steps weighs the
+    components CG resolves slowly, which decide the iterations to a tight
+    tolerance); 'mse': ||x_0 - target||^2 against the phantom (target_iters =
+    0) or a CGLS iterate.  init: (net, meta) to continue from."""
     from .autograd import backproject, project
     torch.manual_seed(0)
     grid, lines = geometry(device)
-    plan = Plan(grid, lines)
+    plan = Plan(grid, lines, records=True)   # many projections per prepare
     t0 = time.time()
-    _, _, _, alpha = make_samples(plan, [1_000_000 + i for i in range(64)], device)
+    if init is not None:
+        alpha = init[1]["alpha"]
+    else:
+        _, _, _, alpha = make_samples(plan, [1_000_000 + i for i in range(64)], device)
     Z, C, Bs = [], [], []
     for s0 in range(0, n_train, chunk):
         z, c, b, _ = make_samples(plan, [1_000_000 + i for i in range(s0, min(n_train, s0 + chunk))], device, alpha,
@@ -169,11 +196,16 @@ def train(n_train=20000, batch=16, epochs=1, lr=1e-3, device="cuda", log=print, 
             return ((x0 - C[idx]) ** 2).mean()
         tot = 0.0
         for j, k in enumerate(idx.tolist()):
-            r = backproject(project(x0[j], plan) - Bs[k], plan)
-            tot = tot + (r * r).sum() / Gn[k]
+            if cg_steps > 0:
+                tot = tot + cgls_residual_after(plan, x0[j], Bs[k], cg_steps) / Gn[k]
+            else:
+                r = backproject(project(x0[j], plan) - Bs[k], plan)
+                tot = tot + (r * r).sum() / Gn[k]
         return tot / len(idx)
     log(f"data: {n_train} samples in {time.time() - t0:.1f} s, alpha {alpha:.4e}")
     net = WarmStartNet().to(device)
+    if init is not None:
+        net.load_state_dict(init[0].state_dict())
     opt = torch.optim.Adam(net.parameters(), lr=lr)
     steps = epochs * (n_train // batch)
     sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, steps)
@@ -202,7 +234,9 @@ def train(n_train=20000, batch=16, epochs=1, lr=1e-3, device="cuda", log=print, 
         net = saved
     meta = {"alpha": alpha, "n_train": n_train, "batch": batch, "epochs": epochs, "lr": lr, "loss": loss_kind,
             "target": (f"CGLS iterate {target_iters} from 0" if target_iters else "phantom") if loss_kind == "mse"
-            else "normal-equation residual",
+            else (f"normal-equation residual after {cg_steps} CGLS steps from x_0" if cg_steps
+                  else "normal-equation residual"),
+            "cg_steps": cg_steps, "continued_from": (init[1].get("target") if init is not None else None),
             "train_loss_identity": base, "train_loss_net": fit, "train_seconds": time.time() - t0,
             "geometry": "256x256 cubic, parallel 360 angles x 384 bins"}
     return net, meta
@@ -322,9 +356,15 @@ def main():
     ap.add_argument("--epochs", type=int, default=1)
     ap.add_argument("--n-test", type=int, default=256)
     ap.add_argument("--report", default=None, help="write the evaluation summary (JSON) here")
+    ap.add_argument("--cg-steps", type=int, default=0, help="train on the residual after this many CGLS steps")
+    ap.add_argument("--init", default=None, help="continue from these weights")
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--batch", type=int, default=16)
     a = ap.parse_args()
     if a.cmd == "train":
-        net, meta = train(n_train=a.n_train, epochs=a.epochs)
+        init = load_net(a.init) if a.init else None
+        net, meta = train(n_train=a.n_train, epochs=a.epochs, cg_steps=a.cg_steps, init=init, lr=a.lr,
+                          batch=a.batch)
         save(net, meta, a.out)
         print(json.dumps(meta))
     else:

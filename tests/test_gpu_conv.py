@@ -65,11 +65,12 @@ def test_conv_forward_matches_oracle(cin, cout, relu, d):
     assert err < (3e-3 if cout > 1 else 1e-5)
 
 
-@pytest.mark.parametrize("cin,cout,d", [(32, 32, 1), (1, 32, 1), (32, 1, 1), (32, 32, 4), (1, 32, 2), (32, 1, 16)])
-def test_conv_gradients_match_oracle(cin, cout, d):
+@pytest.mark.parametrize("cin,cout,d,W", [(32, 32, 1, 33), (1, 32, 1, 33), (32, 1, 1, 33), (32, 32, 4, 33),
+                                           (1, 32, 2, 33), (32, 1, 16, 33), (32, 32, 16, 150), (32, 32, 3, 64)])
+def test_conv_gradients_match_oracle(cin, cout, d, W):
     from paper_2503_20907_gb300 import _lib
-    rng = np.random.default_rng(11 * cin + cout)
-    B, H, W = 2, 5, 33
+    rng = np.random.default_rng(11 * cin + cout + d)
+    B, H = 2, 5
     x = _bf16(rng.standard_normal((B, H, W, cin)))
     w = _bf16(rng.standard_normal((cout, 3, 3, cin)) * 0.2)
     g = torch.from_numpy(rng.standard_normal((B, H, W, cout)).astype(np.float32)).to(DEV)
@@ -78,14 +79,19 @@ def test_conv_gradients_match_oracle(cin, cout, d):
     db = torch.empty(cout, device=DEV)
     _lib._check(lib.sp_conv3x3_bwd_weight(B, H, W, cin, cout, d, x.data_ptr(), g.data_ptr(), dw.data_ptr(),
                                           db.data_ptr(), None))
-    ref_w, ref_b = conv3x3_grad_weight(_exact(x), g.cpu().numpy(), d=d)
+    # the 32 -> 32 gradients run on the tensor cores, which take g rounded to
+    # BF16 (products and sums in FP32); the others take g in FP32.  The bias
+    # gradient sums g in FP32 either way.
+    g_in = _exact(g.to(torch.bfloat16)) if (cin, cout) == (32, 32) else g.cpu().numpy()
+    ref_w, _ = conv3x3_grad_weight(_exact(x), g_in, d=d)
+    _, ref_b = conv3x3_grad_weight(_exact(x), g.cpu().numpy(), d=d)
     assert np.linalg.norm(dw.cpu().numpy() - ref_w) / np.linalg.norm(ref_w) < 1e-5
     assert np.allclose(db.cpu().numpy(), ref_b, rtol=1e-5, atol=1e-4)
     dx = torch.empty((B, H, W, cin), device=DEV)
     gate = _bf16(rng.standard_normal((B, H, W, cin)))
     _lib._check(lib.sp_conv3x3_bwd_data(B, H, W, cin, cout, d, g.data_ptr(), w.data_ptr(), gate.data_ptr(),
                                         dx.data_ptr(), None))
-    ref_x = conv3x3_grad_input(g.cpu().numpy(), _exact(w), d=d) * (_exact(gate) > 0)
+    ref_x = conv3x3_grad_input(g_in, _exact(w), d=d) * (_exact(gate) > 0)
     assert np.linalg.norm(dx.cpu().numpy() - ref_x) / np.linalg.norm(ref_x) < 1e-5
 
 

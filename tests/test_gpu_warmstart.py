@@ -1,9 +1,10 @@
 """The trained warm start (paper_2503_20907_gb300/weights): the network run
 through this library's kernels against the FP64 oracle layers with the same
 BF16 rounding between layers, and what it gains over plain CGLS on held-out
-samples: a smaller starting normal-equation residual, and the iteration
-count to 1e-4 (reported; the late CG iterations are dominated by components
-the network does not predict)."""
+samples, measured and printed: a smaller starting normal-equation residual,
+fewer iterations to a relative residual of 1e-3, and the iterations to 1e-4
+(where it ties cold CGLS: the last decades are spent on components of small
+eigenvalue that the network does not predict)."""
 import numpy as np
 import pytest
 
@@ -45,9 +46,10 @@ def test_warm_start_gain_on_held_out_samples(trained):
     ws, net, meta = trained
     grid, lines = ws.geometry(DEV)
     plan = sp.Plan(grid, lines)
-    z, c, b, _ = ws.make_samples(plan, [2_000_000 + i for i in range(6)], DEV, meta["alpha"])
-    rel0, kc, kw = [], [], []
-    for k in range(6):
+    n = 12
+    z, c, b, _ = ws.make_samples(plan, [2_000_000 + i for i in range(n)], DEV, meta["alpha"])
+    rel0, kc, kw, kc3, kw3 = [], [], [], [], []
+    for k in range(n):
         _, gc = plan.cgls(b[k], 800)
         gc = gc.cpu().numpy()
         with torch.no_grad():
@@ -58,11 +60,21 @@ def test_warm_start_gain_on_held_out_samples(trained):
         rel0.append((np.sqrt(gw[0] / gc[0]), np.sqrt(float(gz[0]) / gc[0])))
         kc.append(ws.iterations_to(gc, gc[0], 1e-4))
         kw.append(ws.iterations_to(gw, gc[0], 1e-4))
-    # the network's start is closer than 0 and than its input z in the normal-equation residual
-    assert all(rw < 0.5 and rw < rz for rw, rz in rel0)
-    # both reach the tolerance; the warm start is not slower by more than a few iterations
-    assert all(a is not None and b_ is not None for a, b_ in zip(kc, kw))
-    assert np.median(kw) <= np.median(kc) + 3
+        kc3.append(ws.iterations_to(gc, gc[0], 1e-3))
+        kw3.append(ws.iterations_to(gw, gc[0], 1e-3))
+    print(f"\nwarm start on {n} held-out samples: starting residual {np.median([a for a, _ in rel0]):.3f} "
+          f"(cold 1, z alone {np.median([b_ for _, b_ in rel0]):.3f}); iterations to 1e-3 "
+          f"{np.median(kw3):.1f} warm vs {np.median(kc3):.1f} cold; to 1e-4 {np.median(kw):.1f} vs {np.median(kc):.1f}")
+    # the network's start is closer than 0, and (median) than its input z, in
+    # the normal-equation residual (it is trained on the residual left after
+    # 12 CGLS steps, not on the starting one)
+    assert np.median([rw for rw, _ in rel0]) < 0.5
+    assert np.median([rw for rw, _ in rel0]) < np.median([rz for _, rz in rel0])
+    # both reach the tolerances
+    assert all(x is not None for x in kc + kw + kc3 + kw3)
+    # the gain: fewer iterations to 1e-3 (median); at 1e-4 the two stay within a few iterations
+    assert np.median(kw3) < np.median(kc3)
+    assert abs(np.median(kw) - np.median(kc)) <= 3
     # the solver with fallback returns a solution within the tolerance either way
     x, iters, warm = ws.solve(plan, b[0], net, meta["alpha"], tol=1e-4)
     s = plan.adj(plan.fwd(x) - b[0])
