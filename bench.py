@@ -287,8 +287,10 @@ def cg_oracle_sample(sp, dev, n=64, iters=100):
     og = oracle.Grid(W.n, W.n, W.degree, W.h)
     b, _ = workloads.transmission_data(oracle.forward(og, W.coef.astype(np.float64), th, yy), seed=3)
     b32 = b.astype(np.float32)
+    nt = os.cpu_count() or 1   # explicit: an earlier one-core sample leaves OpenMP at one thread
     t0 = time.perf_counter()
-    _, _, kept = cgls(lambda x: oracle.forward(og, x, th, yy), lambda p: oracle.adjoint(og, p, th, yy),
+    _, _, kept = cgls(lambda x: oracle.forward(og, x, th, yy, threads=nt),
+                      lambda p: oracle.adjoint(og, p, th, yy, threads=nt),
                       b32.astype(np.float64), np.zeros((W.n, W.n)), iters, keep=range(1, iters + 1))
     t_orc = time.perf_counter() - t0
     plan = sp.Plan(sp.Grid(W.n, W.n, W.degree, W.h),
@@ -302,7 +304,7 @@ def cg_oracle_sample(sp, dev, n=64, iters=100):
         err.append(float(np.linalg.norm(x.cpu().numpy().astype(np.float64) - ref) / np.linalg.norm(ref)))
     plan.close()
     return {"workload": f"64x64 crop of {WORKLOAD} ({th.size} lines), transmission data, Poisson seed 3, x0 = 0",
-            "oracle_seconds_100_iters": t_orc, "cores": oracle.max_threads(),
+            "oracle_seconds_100_iters": t_orc, "cores": nt,
             "rel_err_vs_oracle_per_iter": [float(f"{e:.3g}") for e in err],
             "max_rel_err_k_le_5": max(err[:5])}
 
@@ -628,13 +630,14 @@ def run_ours(args, rank, ws, local):
     if warm is not None:
         line["warm_start"] = warm
     if ws == 1 and not args.no_cpu_baseline and wl.name == WORKLOAD:
-        cb = oracle_sample(wl, nf=120000, npix=1600)   # ~10 s on 16 host cores
+        ncpu = os.cpu_count() or 1
+        cb = oracle_sample(wl, nf=120000, npix=1600, threads=ncpu)   # ~10 s on 16 host cores
         cb.pop("seconds", None)
+        if cg is not None:
+            line["cg"]["vs_oracle_cgls"] = cg_oracle_sample(sp, dev)
         one = oracle_sample(wl, nf=4000, npix=60, threads=1)   # ~5 s on one core
         cb["one_core"] = {"value": one["value"], "sample": one["sample"]}
         line["cpu_baseline"] = cb
-        if cg is not None:
-            line["cg"]["vs_oracle_cgls"] = cg_oracle_sample(sp, dev)
     print(json.dumps(line), flush=True)
 
 

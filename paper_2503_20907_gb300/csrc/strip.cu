@@ -286,9 +286,9 @@ __device__ float strip_tie_line(const LineHdr &H, const float *tabw, int S0, int
 // One line over the strip rows [S0, S1).  Forward (ADJ false): returns this
 // lane's part of sum_k c_k phi (no factor h).  Adjoint: adds hp * phi into the
 // strip.  tabw is the line's table in shared memory; ent_t / ent_p hold the
-// warp's sorted row records (t, strip offset of candidate 0).  CONCAT: the
-// adjoint's phase B schedule over the concatenated segments (below).
-template <int DEG, bool ADJ, bool CONCAT = ADJ, bool FIX = false, int RM = kRecNone>
+// warp's sorted row records (t, strip offset of candidate 0).  FIX: the
+// adjoint's fixed-point strip (hpS = hp S); RM: the row-record mode.
+template <int DEG, bool ADJ, bool FIX = false, int RM = kRecNone>
 __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, int *ent_p, float *strip, const int *clo,
                             int S0, int S1, int lane, const float *__restrict__ src, float *dst, int Nq,
                             int *err, float hp, float hpS, unsigned char *&rp, const unsigned char *rend)
@@ -453,43 +453,18 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
         // ---- B: lane per (candidate, row slot), four rows per step
         if (lane_on) {
             f2 C[NC];
-            if constexpr (ADJ && CONCAT) {
-                // The segments are contiguous and padded to whole groups of 4
-                // records, so slot sl takes groups sl, sl + nsl, ... of their
-                // concatenation (no slot idles at the end of a segment: each
-                // idle step would still cost its four reductions) and loads
-                // the polynomial of its group's interval on entering a segment.
-                const int R = segb[NS - 1] + segn[NS - 1];
-                int nb = 0;   // end of the segment whose polynomial is loaded
-                for (int e = 4 * sl; e < R; e += 4 * nsl) {
-                    if (e >= nb) {
-                        int q = 0, sb = 0, sn = 0;
+            // one interval at a time (an interval's last step may leave some
+            // row slots idle; walking the concatenated intervals instead costs
+            // a segment test per step and was slower in both directions once
+            // the adjoint's reductions became integer ones)
 #pragma unroll
-                        for (int qq = 1; qq < NS; ++qq)
-                            if (segb[qq] <= e) q = qq;
-#pragma unroll
-                        for (int qq = 0; qq < NS; ++qq)
-                            if (qq == q) { sb = segb[qq]; sn = segn[qq]; }
-                        nb = sb + sn;
-                        load_poly<DEG, ADJ, FIX>(tabw, q, ci, FIX ? hpS : hp, H.a_corr, C);
-                    }
+            for (int q = 0; q < NS; ++q) {
+                const int n = segn[q];
+                if (n == 0) continue;
+                load_poly<DEG, ADJ, FIX>(tabw, q, ci, FIX ? hpS : hp, H.a_corr, C);
+                const int end = segb[q] + n;
+                for (int e = segb[q] + 4 * sl; e < end; e += 4 * nsl)
                     run_group<DEG, ADJ, FIX>(C, ent_t, ent_p, e, strip, coloff, acc2);
-                }
-            } else {
-                // one interval at a time: the forward's steps are cheap enough
-                // that the per-step segment test of the schedule above costs
-                // more than the idle slots it saves (and the batch queue
-                // kernel, which carries every degree in one register budget,
-                // keeps this schedule for the adjoint too)
-#pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    const int n = segn[q];
-                    if (n == 0) continue;
-                    load_poly<DEG, ADJ, FIX>(tabw, q, ci, FIX ? hpS : hp, H.a_corr, C);
-                    const int end = segb[q] + n;
-                    for (int e = segb[q] + 4 * sl; e < end; e += 4 * nsl)
-                        run_group<DEG, ADJ, FIX>(C, ent_t, ent_p, e, strip, coloff, acc2);
-                }
             }
         }
         __syncwarp();
@@ -508,7 +483,7 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
 // transposed image).
 // One chunk (view v, bins j0..j0+31) of one instance; smem is the CTA's
 // dynamic shared memory (kSmemBytes).
-template <int DEG, bool ADJ, bool CONCAT = ADJ, int RM = kRecNone>
+template <int DEG, bool ADJ, int RM = kRecNone>
 __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g, const LinesDev L,
                                             const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
                                             const float *__restrict__ coef, const float *__restrict__ coefT,
@@ -748,11 +723,11 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                     const unsigned char *rend = lrec ? lrec + rec_cap : nullptr;
                     float part;
                     if (ADJ && fixed)
-                        part = strip_line<DEG, ADJ, CONCAT, true, RM>(H, tabbuf + buf * kTabFloats, ent_t, ent_p, strip,
+                        part = strip_line<DEG, ADJ, true, RM>(H, tabbuf + buf * kTabFloats, ent_t, ent_p, strip,
                                                                       clo, S0, S1, lane, src, dst, Nq, err, hp,
                                                                       hp * fscale, rp, rend);
                     else
-                        part = strip_line<DEG, ADJ, CONCAT, false, RM>(H, tabbuf + buf * kTabFloats, ent_t, ent_p,
+                        part = strip_line<DEG, ADJ, false, RM>(H, tabbuf + buf * kTabFloats, ent_t, ent_p,
                                                                        strip, clo, S0, S1, lane, src, dst, Nq, err, hp,
                                                                        0.f, rp, rend);
                     if (!ADJ && rmode != kRecWrite) {
@@ -816,7 +791,7 @@ strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float
              unsigned char *rec, long long rec_cap)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    strip_chunk<DEG, ADJ, ADJ, RM>(smem, g, L, hdr, tabs, coef, coefT, sino, out, outT, chunks_per_view, vec, err,
+    strip_chunk<DEG, ADJ, RM>(smem, g, L, hdr, tabs, coef, coefT, sino, out, outT, chunks_per_view, vec, err,
                                    (int)blockIdx.x, rec, rec_cap);
 }
 
@@ -846,15 +821,15 @@ strip_queue_kernel(const StripJob *__restrict__ jobs, int njobs, long long total
         const int local = (int)(c - J->chunk0);
         switch (J->g.kdeg) {
         case 1:
-            strip_chunk<1, ADJ, false>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
+            strip_chunk<1, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
                                 J->cpv, J->vec, J->err, local);
             break;
         case 2:
-            strip_chunk<2, ADJ, false>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
+            strip_chunk<2, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
                                 J->cpv, J->vec, J->err, local);
             break;
         default:
-            strip_chunk<3, ADJ, false>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
+            strip_chunk<3, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
                                 J->cpv, J->vec, J->err, local);
             break;
         }
