@@ -275,7 +275,9 @@ def cg_oracle_sample(sp, dev, n=64, iters=100):
     it: FP64 oracle CGLS (100 iterations) on the 64 x 64 crop of the 512^2
     cubic fan scan (transmission data, Poisson seed 3), timed on the host
     cores; then the relative L2 error of each GPU iterate x_k (spline_plan_cgls
-    run k iterations from x_0 = 0) against the oracle's x_k, k = 1..100."""
+    run k iterations from x_0 = 0) against the oracle's x_k, k = 1..100, in
+    the image and in the data (||A (x_k - x_k^orc)|| / ||A x_k^orc||, A the
+    oracle's forward), and both relative normal-equation residuals."""
     import numpy as np
     import torch
     import oracle
@@ -289,24 +291,34 @@ def cg_oracle_sample(sp, dev, n=64, iters=100):
     b32 = b.astype(np.float32)
     nt = os.cpu_count() or 1   # explicit: an earlier one-core sample leaves OpenMP at one thread
     t0 = time.perf_counter()
-    _, _, kept = cgls(lambda x: oracle.forward(og, x, th, yy, threads=nt),
-                      lambda p: oracle.adjoint(og, p, th, yy, threads=nt),
-                      b32.astype(np.float64), np.zeros((W.n, W.n)), iters, keep=range(1, iters + 1))
+    _, gam_o, kept = cgls(lambda x: oracle.forward(og, x, th, yy, threads=nt),
+                          lambda p: oracle.adjoint(og, p, th, yy, threads=nt),
+                          b32.astype(np.float64), np.zeros((W.n, W.n)), iters, keep=range(1, iters + 1))
     t_orc = time.perf_counter() - t0
     plan = sp.Plan(sp.Grid(W.n, W.n, W.degree, W.h),
                    sp.Lines.fan(torch.from_numpy(geo.view_angle).to(dev), geo.dso, geo.dod, geo.n_det,
                                 geo.det0, geo.ddet))
     bt = torch.from_numpy(b32).to(dev)
-    err = []
+    err, err_data = [], []
     for k in range(1, iters + 1):
         x, _ = plan.cgls(bt, k, history=False)
         ref = kept[k]
-        err.append(float(np.linalg.norm(x.cpu().numpy().astype(np.float64) - ref) / np.linalg.norm(ref)))
+        d = x.cpu().numpy().astype(np.float64) - ref
+        err.append(float(np.linalg.norm(d) / np.linalg.norm(ref)))
+        err_data.append(float(np.linalg.norm(oracle.forward(og, d, th, yy, threads=nt))
+                              / np.linalg.norm(oracle.forward(og, ref, th, yy, threads=nt))))
+    _, gam_g = plan.cgls(bt, iters)
+    gam_g = gam_g.cpu().numpy()
     plan.close()
+    at = [k for k in (1, 2, 5, 10, 20, 50, 100) if k <= iters]
     return {"workload": f"64x64 crop of {WORKLOAD} ({th.size} lines), transmission data, Poisson seed 3, x0 = 0",
             "oracle_seconds_100_iters": t_orc, "cores": nt,
             "rel_err_vs_oracle_per_iter": [float(f"{e:.3g}") for e in err],
-            "max_rel_err_k_le_5": max(err[:5])}
+            "rel_data_err_vs_oracle_per_iter": [float(f"{e:.3g}") for e in err_data],
+            "max_rel_err_k_le_5": max(err[:5]),
+            "rel_residual_normal_eq": {str(k): {"gpu": float(f"{np.sqrt(gam_g[k] / gam_g[0]):.4g}"),
+                                                "oracle": float(f"{np.sqrt(gam_o[k] / gam_o[0]):.4g}")}
+                                       for k in at}}
 
 
 def run_reference(args, rank, ws):
