@@ -525,6 +525,36 @@ def run_ours(args, rank, ws, local):
                              "adj_choice": {1: "strip scatter", 2: "warp scatter", 3: "gather"}.get(a_path)}
             p2.close()
 
+    # A free line list: 10^6 random chords (both endpoints uniform on the
+    # circle of radius 0.75 N) on the same grid, on the strip kernels through
+    # their sorted order against the warp-per-line kernels (autotuner timings),
+    # and its prepare (line setup, tables, sort) timed alone.
+    free = None
+    if not args.no_schemes:
+        src, dst = workloads.random_lines_circle(1_000_000, 0.75 * wl.n, 17)
+        lf = sp.Lines.points(torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev))
+        pf = sp.Plan(grid, lf, prepare=True)
+        sf = pf.fwd(coef)
+        f_path, a_path, ms = pf.autotune(coef, sf)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pt = []
+        for _ in range(5):
+            e0.record(stream)
+            pf.prepare(stream)
+            e1.record(stream)
+            e1.synchronize()
+            pt.append(e0.elapsed_time(e1))
+        pf.set_paths(1, 1)
+        pf.fwd(coef)
+        pf.adj(sf)
+        torch.cuda.synchronize()
+        free = {"workload": f"1e6 random chords on the {wl.n}^2 cubic grid (endpoints on the circle of radius 0.75 N)",
+                "fwd_strip_ms": ms[0], "fwd_warp_ms": ms[1], "adj_strip_ms": ms[2], "adj_warp_ms": ms[3],
+                "prepare_ms": statistics.median(pt[1:]), "slow_rows": pf.slow_rows(),
+                "mrays_per_s_fwd_adj": 1.0 / (1e-3 * (min(ms[0], ms[1]) + min(ms[2], ms[3]))),
+                "choice": [{1: "strip", 2: "warp"}.get(f_path), {1: "strip", 2: "warp", 3: "gather"}.get(a_path)]}
+        pf.close()
+
     # The same step with row records kept by the plan (written by prepare,
     # read by both projections), as iterative solvers use it.
     rec = None
@@ -633,6 +663,8 @@ def run_ours(args, rank, ws, local):
     }
     if schemes:
         line["adjoint_schemes"] = schemes
+    if free is not None:
+        line["free_line_list"] = free
     if rec is not None:
         line["with_row_records"] = rec
     if cg is not None:

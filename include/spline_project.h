@@ -166,7 +166,8 @@ sp_status spline_visited(const sp_grid *grid, const sp_lines *lines, int32_t *co
  * (iterative reconstruction, autograd) skip the setup.  The steps of one pass
  * of the projector are then separate calls:
  *   spline_plan_prepare  line setup (eq. rayparam) and footprint tables
- *                        (Prop. 1, eq. xsa), and, where the plan keeps
+ *                        (Prop. 1, eq. xsa), for THETA_Y and POINTS lists
+ *                        the strip kernels' line order, and, where the plan keeps
  *                        them, the row records: for every major-axis row of
  *                        every line, the position of its run of nodes and
  *                        the argument of its footprint polynomials (the
@@ -218,7 +219,10 @@ sp_status spline_plan_cgls(sp_plan *plan, const float *b, float *x, int32_t iter
                            double *gamma_hist, void *stream);
 /*
  * Kernel choice of a plan, per direction: 0 = automatic (the strip kernels
- * for PARALLEL and FAN lines of degree >= 1, else the general kernels),
+ * for degree >= 1, else the general kernels; THETA_Y and POINTS lists reach
+ * the strip kernels through an order that prepare sorts them into: by major
+ * axis, direction and offset, so that 32 consecutive lines are nearly
+ * parallel neighbours),
  * 1 = strip kernels where they apply (ray-driven: the adjoint scatters into
  * shared-memory strips), 2 = general kernels (warp per line; the adjoint
  * scatters with global atomics), and for the adjoint only 3 = pixel-driven
@@ -244,7 +248,7 @@ sp_status spline_plan_autotune(sp_plan *plan, const float *coef, const float *si
 /*
  * Batches: several independent instances (each its own grid, basis, degree
  * and line list, sizes free) projected together.  Instances on the strip
- * kernels (parallel and fan lists; degree >= 1 unless the path is set or
+ * kernels (any line list; degree >= 1 unless the path is set or
  * tuned to them; path not forced to the
  * general kernels) share one persistent launch that takes chunks of 32
  * lines of any of them from a work queue; the others are forked over 8
@@ -292,8 +296,7 @@ int64_t spline_plan_record_bytes(const sp_plan *plan);
 /*
  * keep = 1: the plan keeps row records, written by every later
  * spline_plan_prepare (the plan must be prepared again before it projects);
- * SP_EUNSUPPORTED unless the lines are a parallel or fan beam and the degree
- * is >= 1, SP_ENOMEM if they would take more than a quarter of the device's
+ * SP_EUNSUPPORTED unless the degree is >= 1, SP_ENOMEM if they would take more than a quarter of the device's
  * free memory or 16 GiB (cudaMalloc).  keep = 0 frees them (synchronises the
  * device).
  */

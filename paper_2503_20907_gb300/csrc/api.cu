@@ -140,15 +140,25 @@ int64_t table_count(const spx::LinesDev &L)
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Line records and footprint tables for (grid, lines) in the workspace.
-// Scratch of the strip forward: transposed coefficients, then the slow-row counter.
+// Scratch of the strip kernels: transposed coefficients, the slow-row
+// counter, then (free line lists) the chunk order and its sort's scratch.
 size_t extra_bytes(const spx::GridDev &g, const spx::LinesDev &L)
 {
-    return spx::strip_supported(g, L) ? spx::strip_scratch_bytes(g) + 256 : 0;
+    if (!spx::strip_supported(g, L)) return 0;
+    return align_up(spx::strip_scratch_bytes(g)) + 256 +
+           (spx::strip_needs_order(L) ? spx::line_order_bytes(L.m) : 0);
 }
 
 int *slow_counter(const spx::GridDev &g, void *extra)
 {
     return reinterpret_cast<int *>(static_cast<char *>(extra) + align_up(spx::strip_scratch_bytes(g)));
+}
+
+// Where the chunk order of a free line list lives (NULL for other kinds).
+void *order_area(const spx::GridDev &g, const spx::LinesDev &L, void *extra)
+{
+    if (!extra || !spx::strip_needs_order(L) || !spx::strip_supported(g, L)) return nullptr;
+    return static_cast<char *>(extra) + align_up(spx::strip_scratch_bytes(g)) + 256;
 }
 
 // Kernel paths: strip kernels (structured geometries, any degree) or the
@@ -196,7 +206,7 @@ size_t rec_bytes_wanted(const spx::GridDev &g, const spx::LinesDev &L)
     return (size_t)L.m * (size_t)spx::strip_rec_line_bytes(g);
 }
 
-sp_status prepare(const spx::GridDev &g, const spx::LinesDev &L, cudaStream_t s,
+sp_status prepare(const spx::GridDev &g, spx::LinesDev &L, cudaStream_t s,
                   spx::LineHdr **hdr, float **tabs, void **extra = nullptr)
 {
     const int64_t nt = table_count(L);
@@ -211,6 +221,13 @@ sp_status prepare(const spx::GridDev &g, const spx::LinesDev &L, cudaStream_t s,
     if (extra) *extra = xb ? static_cast<char *>(ws) + hb + tb : nullptr;
     cudaError_t e = spx::launch_prepare(g, L, *hdr, *tabs, nt, s);
     if (e != cudaSuccess) return cuda_fail(e, "line setup and footprint tables");
+    // free line lists: the chunk order of the strip kernels
+    void *oa = extra ? order_area(g, L, *extra) : nullptr;
+    if (oa) {
+        e = spx::launch_line_order(g, L, *hdr, oa, s);
+        if (e != cudaSuccess) return cuda_fail(e, "line order");
+        L.order = static_cast<const int *>(oa);
+    }
     return SP_OK;
 }
 
@@ -399,6 +416,7 @@ sp_status plan_create(const sp_grid *grid, const sp_lines *lines, sp_plan **plan
     p->hdr = reinterpret_cast<spx::LineHdr *>(mem);
     p->tabs = mem ? reinterpret_cast<float *>(static_cast<char *>(mem) + hb) : nullptr;
     p->extra = (mem && xb) ? static_cast<char *>(mem) + hb + tb : nullptr;
+    p->L.order = static_cast<const int *>(order_area(g, L, p->extra));   // written by prepare
     p->prepared = false;
     p->cg_ws = nullptr;
     p->cg_bytes = 0;
@@ -444,7 +462,7 @@ sp_status spline_plan_set_records(sp_plan *plan, int32_t keep)
     }
     if (plan->rec.base) return SP_OK;
     if (rec_bytes_wanted(plan->g, plan->L) == 0)
-        return fail(SP_EUNSUPPORTED, "row records exist only for parallel and fan beams of degree >= 1");
+        return fail(SP_EUNSUPPORTED, "row records exist only for B-spline or box-spline grids of degree >= 1");
     if (!plan_alloc_records(plan)) return fail(SP_ENOMEM, "row records do not fit in device memory");
     plan->prepared = false;   // records are written by the next prepare
     return SP_OK;
@@ -458,6 +476,10 @@ sp_status spline_plan_prepare(sp_plan *plan, void *stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = spx::launch_prepare(plan->g, plan->L, plan->hdr, plan->tabs, table_count(plan->L), s);
     if (e != cudaSuccess) return cuda_fail(e, "line setup and footprint tables");
+    if (plan->L.order) {
+        e = spx::launch_line_order(plan->g, plan->L, plan->hdr, const_cast<int *>(plan->L.order), s);
+        if (e != cudaSuccess) return cuda_fail(e, "line order");
+    }
     if (plan->rec.base) {
         e = spx::launch_strip_record(plan->g, plan->L, plan->hdr, plan->tabs, plan->rec, s);
         if (e != cudaSuccess) return cuda_fail(e, "row records");

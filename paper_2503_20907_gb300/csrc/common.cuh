@@ -103,7 +103,17 @@ struct LinesDev {
     int64_t m;
     const float *theta, *y, *src, *dst, *view;
     float det0, ddet, dso, dod;
+    // Free line lists (THETA_Y, POINTS) on the strip kernels: the line indices
+    // in chunk order (sorted by major axis, direction and offset; order.cu),
+    // else NULL (parallel and fan beams take their lines view by view).
+    const int *order;
 };
+
+// The chunk layout of the strip kernels: n_view "views" of n_det lines each,
+// cut into chunks of 32 consecutive lines.  A sorted free list is one view
+// of m lines.
+__host__ __device__ __forceinline__ int64_t chunk_views(const LinesDev &L) { return L.order ? 1 : L.n_view; }
+__host__ __device__ __forceinline__ int64_t chunk_bins(const LinesDev &L) { return L.order ? L.m : L.n_det; }
 
 // Exactly-rounded u_0 of row r for a given step count k:
 // u_0 = U0 + dr*rho - k*a, with the hi products exact.
@@ -278,8 +288,19 @@ struct StripRec {
     long long line_bytes;
 };
 
+// Free line lists in strip-kernel order (order.cu): the key of every line
+// (major axis, then direction, then the position of its run at the grid's
+// middle row) and a stable radix sort of the line indices by it.  `area`
+// holds line_order_bytes(m); the order (m ints) is at its start, the rest is
+// scratch of the sort.
+size_t line_order_bytes(int64_t m);
+cudaError_t launch_line_order(const GridDev &g, const LinesDev &L, const LineHdr *hdr, void *area, cudaStream_t s);
+// Whether the strip kernels take the lines of L through a sorted order.
+inline bool strip_needs_order(const LinesDev &L) { return L.kind == SP_LINES_THETA_Y || L.kind == SP_LINES_POINTS; }
+
 // Forward projection with coefficient strips in shared memory (strip.cu), for
-// parallel and fan beams (any degree).  `scratch` holds strip_scratch_bytes;
+// parallel and fan beams and sorted free line lists (any degree; L.order set
+// for the latter).  `scratch` holds strip_scratch_bytes;
 // `slow_rows` counts rows whose run fell outside the staged window.  With
 // `rec` (written by launch_strip_record for the same lines) the row records
 // are read instead of recomputed.

@@ -177,6 +177,9 @@ __device__ __forceinline__ void table_copy_async(float *dst, const float *src, i
     for (int i = lane; i < n16; i += 32) cp_async16(dst + 4 * i, src + 4 * i);
 }
 
+// floor(a / b) for b > 0.
+__device__ __forceinline__ long long floor_div(long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
 // Prefetch `bytes` from p towards L2 (one 128-byte line per lane and pass).
 __device__ __forceinline__ void prefetch_span_l2(const unsigned char *p, int bytes, int lane)
 {
@@ -513,18 +516,31 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
     int *ent_p = reinterpret_cast<int *>(ent_t + kEntCap);
     const int v = chunk / chunks_per_view, cb = chunk - v * chunks_per_view;
     const int j0 = cb * kChunk;
-    const int nl = min(kChunk, L.n_det - j0);
-    const int64_t line0 = (int64_t)v * L.n_det + j0;
+    const int64_t nd = chunk_bins(L);
+    const int nl = (int)min((int64_t)kChunk, nd - j0);
+    // position of the chunk's first line (in the sorted order for free lists;
+    // records are kept by position), and lane l's line index in every warp
+    const int64_t line0 = (int64_t)v * nd + j0;
+    const int my_line = lane < nl ? (L.order ? __ldg(L.order + line0 + lane) : (int)(line0 + lane)) : 0;
 
     if (!ADJ && threadIdx.x < kChunk) line_acc[threadIdx.x] = 0.f;
     if (threadIdx.x < kChunk) rec_off[threadIdx.x] = 0;
     if (!ADJ && threadIdx.x < kDummy) strip[kSlabRows * kPitch + threadIdx.x] = 0.f;
     // the chunk's line records into shared memory, its tables towards L2
-    for (int i = threadIdx.x; i < nl * 4; i += kThreads)
-        reinterpret_cast<int4 *>(hdr_s)[i] = __ldg(reinterpret_cast<const int4 *>(hdr + line0) + i);
+    // (lines other than parallel beams have one table each, indexed by line)
+    static_assert(kChunk * 4 <= kThreads, "one pass over the chunk's line records");
+    {
+        const int src = __shfl_sync(0xffffffffu, my_line, (threadIdx.x >> 2) & 31);
+        if ((int)threadIdx.x < nl * 4)
+            reinterpret_cast<int4 *>(hdr_s)[threadIdx.x] =
+                __ldg(reinterpret_cast<const int4 *>(hdr + src) + (threadIdx.x & 3));
+    }
     if (L.kind != SP_LINES_PARALLEL)
-        for (int i = threadIdx.x; i < nl * kTabLines; i += kThreads)
-            prefetch_l2(tabs + (line0 + i / kTabLines) * (int64_t)kTabFloats + (i % kTabLines) * 32);
+        for (int i0 = 0; i0 < kChunk * kTabLines; i0 += kThreads) {
+            const int i = i0 + threadIdx.x;
+            const int src = __shfl_sync(0xffffffffu, my_line, min(i / kTabLines, kChunk - 1));
+            if (i < nl * kTabLines) prefetch_l2(tabs + (int64_t)src * kTabFloats + (i % kTabLines) * 32);
+        }
     if constexpr (ADJ) {
         // The chunk's fixed-point scale S (a power of two; see the top of the
         // file): misc[5] = 1 if the strip accumulates in fixed point, misc[6]
@@ -532,7 +548,7 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
         // large or small that S leaves a safe exponent range, keep the float
         // reductions.
         if (warp == 0) {
-            const float pv = lane < nl ? sino[line0 + lane] : 0.f;
+            const float pv = lane < nl ? sino[my_line] : 0.f;
             const bool bad = !isfinite(pv);
             float pm = fabsf(pv);
 #pragma unroll
@@ -568,7 +584,7 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                 mine = !(H.flags & kEmpty) && (((H.flags & kVert) != 0) == (axis == 0)) && H.r_end > H.r_begin;
                 // (with kept records the groups must be those of the record pass,
                 // so lines with p = 0 stay in them and are skipped below)
-                if (ADJ && mine && rmode == kRecNone) mine = sino[line0 + lane] != 0.f;
+                if (ADJ && mine && rmode == kRecNone) mine = sino[my_line] != 0.f;
             }
             const unsigned mask = __ballot_sync(0xffffffffu, mine);
             if (lane == 0) {
@@ -610,7 +626,30 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                 R1 = max(R1, __shfl_xor_sync(0xffffffffu, R1, o2));
             }
             int wmax = 0;
-            {
+            // free lists: the extreme run columns over all lines of the group
+            // at the first and the last row (la..ha, lb..hb); between them the
+            // window follows the chords, which bound the runs: each run moves
+            // linearly with the row, so the lowest start is concave in the row
+            // and the highest end convex
+            int la = 0, ha = 0, lb = 0, hb = 0;
+            if (L.order) {
+                la = lb = INT_MAX;
+                ha = hb = INT_MIN;
+                if ((gmask >> lane) & 1u) {
+                    const LineHdr &Hx = hdr_s[lane];
+                    const float ia = 1.0f / Hx.a;
+                    run_columns(Hx, ia, R0, la, ha);
+                    run_columns(Hx, ia, R1 - 1, lb, hb);
+                }
+#pragma unroll
+                for (int o2 = 16; o2 > 0; o2 >>= 1) {
+                    la = min(la, __shfl_xor_sync(0xffffffffu, la, o2));
+                    ha = max(ha, __shfl_xor_sync(0xffffffffu, ha, o2));
+                    lb = min(lb, __shfl_xor_sync(0xffffffffu, lb, o2));
+                    hb = max(hb, __shfl_xor_sync(0xffffffffu, hb, o2));
+                }
+                wmax = max(ha - la, hb - lb) + 7;
+            } else {
                 int lo1, hi1, lo2, hi2;
                 run_columns(Hf, inv_af, R0, lo1, hi1);
                 run_columns(Hl, inv_al, R0, lo2, hi2);
@@ -637,10 +676,20 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                 // window of each strip row from the two outermost lines of the
                 // group (lines of a view do not cross inside the grid), margin 2
                 for (int rr = threadIdx.x; rr < nrows; rr += kThreads) {
-                    int lo1, hi1, lo2, hi2;
-                    run_columns(Hf, inv_af, S0 + rr, lo1, hi1);
-                    run_columns(Hl, inv_al, S0 + rr, lo2, hi2);
-                    const int lo = min(lo1, lo2) - 2, hi = max(hi1, hi2) + 2;
+                    int lo, hi;
+                    if (L.order) {
+                        // the chords, rounded outwards, margin 3 (a run lies
+                        // within one column of its line)
+                        const long long span = max(R1 - 1 - R0, 1), dr = S0 + rr - R0;
+                        lo = la + (int)floor_div((long long)(lb - la) * dr, span) - 3;
+                        hi = ha - (int)floor_div(-(long long)(hb - ha) * dr, span) + 3;
+                    } else {
+                        int lo1, hi1, lo2, hi2;
+                        run_columns(Hf, inv_af, S0 + rr, lo1, hi1);
+                        run_columns(Hl, inv_al, S0 + rr, lo2, hi2);
+                        lo = min(lo1, lo2) - 2;
+                        hi = max(hi1, hi2) + 2;
+                    }
                     // centred in the usable width, start rounded down to a 16-byte chunk
                     clo[rr] = (lo - max(0, (kWin - (hi - lo + 1)) / 2)) & ~3;
                 }
@@ -688,7 +737,7 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                 // ahead.
                 unsigned wmask = gmask;
                 if (ADJ && rmode == kRecRead) {
-                    const bool nz = lane < nl && sino[line0 + lane] != 0.f;
+                    const bool nz = lane < nl && sino[my_line] != 0.f;
                     wmask &= __ballot_sync(0xffffffffu, nz);
                 }
                 int li = first + warp;
@@ -717,7 +766,7 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                     cp_async_wait<1>();
                     __syncwarp();
                     const LineHdr H = hdr_s[li];
-                    const float hp = ADJ ? g.h * sino[line0 + li] : 0.f;
+                    const float hp = ADJ ? g.h * sino[__shfl_sync(0xffffffffu, my_line, li)] : 0.f;
                     unsigned char *lrec = rec ? rec + (line0 + li) * rec_cap : nullptr;
                     unsigned char *rp = lrec ? lrec + rec_off[li] : nullptr;
                     const unsigned char *rend = lrec ? lrec + rec_cap : nullptr;
@@ -779,7 +828,7 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
     }
     if (!ADJ && rmode != kRecWrite) {
         __syncthreads();
-        if (threadIdx.x < nl) sino[line0 + threadIdx.x] = g.h * line_acc[threadIdx.x];
+        if ((int)threadIdx.x < nl) sino[my_line] = g.h * line_acc[threadIdx.x];   // warp 0: lane = line
     }
 }
 
@@ -891,8 +940,9 @@ cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *h
                                      : strip_kernel<DEG, ADJ, kRecNone>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    const int cpv = (L.n_det + kChunk - 1) / kChunk;
-    const unsigned grid = (unsigned)(L.n_view * cpv);
+    if (strip_needs_order(L) && !L.order) return cudaErrorInvalidValue;   // free lists need their order
+    const int cpv = (int)((chunk_bins(L) + kChunk - 1) / kChunk);
+    const unsigned grid = (unsigned)(chunk_views(L) * cpv);
     // 16-byte staging and flushing: image rows (nx and ny floats) and bases aligned
     const float *img = ADJ ? out : coef;
     const int vec = (g.nx % 4 == 0) && (g.ny % 4 == 0) && ((reinterpret_cast<uintptr_t>(img) & 15) == 0) &&
@@ -923,7 +973,7 @@ StripJob make_strip_job(const GridDev &g, const LinesDev &L, const LineHdr *hdr,
     J.out = adj ? img_out : nullptr;
     J.outT = static_cast<float *>(scratch);
     J.err = err;
-    J.cpv = (L.n_det + kChunk - 1) / kChunk;
+    J.cpv = (int)((chunk_bins(L) + kChunk - 1) / kChunk);
     const void *img = adj ? static_cast<const void *>(img_out) : static_cast<const void *>(img_in);
     J.vec = (g.nx % 4 == 0) && (g.ny % 4 == 0) && ((reinterpret_cast<uintptr_t>(img) & 15) == 0) &&
             ((reinterpret_cast<uintptr_t>(scratch) & 15) == 0);
@@ -931,7 +981,7 @@ StripJob make_strip_job(const GridDev &g, const LinesDev &L, const LineHdr *hdr,
     return J;
 }
 
-int64_t strip_job_chunks(const StripJob &J) { return (int64_t)J.L.n_view * J.cpv; }
+int64_t strip_job_chunks(const StripJob &J) { return chunk_views(J.L) * J.cpv; }
 
 cudaError_t launch_strip_pre(const StripJob &J, bool adj, cudaStream_t s)
 {
@@ -978,7 +1028,7 @@ cudaError_t launch_strip_queue(bool adj, const StripJob *jobs, int njobs, int64_
 
 bool strip_supported(const GridDev &g, const LinesDev &L)
 {
-    return (L.kind == SP_LINES_PARALLEL || L.kind == SP_LINES_FAN) && g.kdeg >= 0;
+    return (L.kind == SP_LINES_PARALLEL || L.kind == SP_LINES_FAN || strip_needs_order(L)) && g.kdeg >= 0;
 }
 
 size_t strip_scratch_bytes(const GridDev &g) { return sizeof(float) * (size_t)g.nx * g.ny + 256; }

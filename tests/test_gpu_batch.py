@@ -51,8 +51,8 @@ def test_batch_matches_plans_and_replays(batch_setup):
         ref = p.adj(s)
         assert float((bk - ref).norm() / ref.norm().clamp_min(1e-30)) < 1e-6
     # the strip-eligible instances ran through the persistent queue kernel
-    n_strip = sum(1 for L, g in zip(lines, grids)
-                  if L.kind in (sp._lib.KIND_PARALLEL, sp._lib.KIND_FAN) and g.degree >= 1)
+    # (parallel and fan beams, and free lists through their sorted order)
+    n_strip = sum(1 for g in grids if g.degree >= 1)
     assert n_strip >= 2
     assert batch.queued(False) == n_strip and batch.queued(True) == n_strip
 
@@ -76,8 +76,6 @@ def test_autotune_choices_keep_parity(batch_setup):
     assert len(paths) == len(ws)
     for (f, a), L, g in zip(paths, lines, grids):
         assert f in (1, 2) and a in (1, 2)
-        if L.kind == sp._lib.KIND_POINTS:
-            assert (f, a) == (2, 2)               # strip kernels do not apply
     out = batch.fwd(coefs)
     back = batch.adj(sinos)
     for k in (1, 3, len(ws) - 1):
@@ -91,8 +89,6 @@ def test_autotune_choices_keep_parity(batch_setup):
 def test_general_and_strip_kernels_agree(batch_setup):
     ws, grids, lines, coefs, batch, plans = batch_setup
     for p, c, L, g in zip(plans, coefs, lines, grids):
-        if L.kind not in (sp._lib.KIND_PARALLEL, sp._lib.KIND_FAN):
-            continue
         p.set_paths(1, 1)
         s1 = p.fwd(c)
         b1 = p.adj(s1)
@@ -106,9 +102,9 @@ def test_general_and_strip_kernels_agree(batch_setup):
 
 def _mixed_instances():
     """Edge cases of the queue: a chunk of fewer than 32 lines, one view, a
-    rectangular grid whose rows are not whole 16-byte chunks, degree 0 and a
-    free line list (both off the queue by default), a grid smaller than the
-    support."""
+    rectangular grid whose rows are not whole 16-byte chunks, degree 0 (off
+    the queue by default), a free line list (on the queue in its sorted
+    order), a grid smaller than the support."""
     rng = np.random.default_rng(77)
     specs = []
     # (grid, lines-maker)
@@ -136,16 +132,16 @@ def test_batch_queue_edge_cases():
     coefs = [torch.rand(g.ny, g.nx, generator=gen).to(DEV) for g in grids]
     sinos = batch.fwd(coefs)
     backs = batch.adj(sinos)
-    assert batch.queued(False) == 3 and batch.queued(True) == 3
+    assert batch.queued(False) == 4 and batch.queued(True) == 4
     for s, b, p, c, sn in zip(sinos, backs, plans, coefs, sinos):
         assert torch.equal(s, p.fwd(c))
         ref = p.adj(sn)
         assert float((b - ref).norm() / ref.norm().clamp_min(1e-30)) < 1e-6
-    # only instances off the queue (degree 0 takes the general kernels unless
-    # tuned or set otherwise): nothing queued, same results
+    # degree 0 (the general kernels unless tuned or set otherwise) beside the
+    # free list: one queued, same results
     b2 = sp.Batch(grids[3:], lines[3:])
     s2 = b2.fwd(coefs[3:])
-    assert b2.queued(False) == 0
+    assert b2.queued(False) == 1
     for s, p, c in zip(s2, plans[3:], coefs[3:]):
         assert torch.equal(s, p.fwd(c))
     # one queued instance alone

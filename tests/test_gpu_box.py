@@ -1,7 +1,7 @@
 """Parity of the CUDA projector with the 3-direction box-spline basis
 (Sec. III.D) against the FP64 oracle: its footprint table, forward and
-adjoint on every line-list kind (the strip kernels for parallel and fan
-beams, the general kernels for the others), the adjoint identity, the
+adjoint on every line-list kind (the strip kernels by default, free lists
+through their sorted order), the adjoint identity, the
 visited set, and the 256 x 256 fan geometry on sampled lines.  Same bar as
 the B-spline projector: relative L2 <= 1e-5."""
 import math
