@@ -354,6 +354,18 @@ const char *sp_last_error(void);
 /* Library version, major*10000 + minor*100 + patch. */
 int32_t sp_version(void);
 
+/*
+ * FP32 throughput of the current device, measured (the denominator of the
+ * projector's roofline; no paper counterpart): a kernel of independent
+ * fused multiply-add chains on every SM, as scalar fma.rn.f32 (packed = 0)
+ * or packed fma.rn.f32x2 (packed = 1), timed with CUDA events on `stream`
+ * after one warm-up launch (best of three).  *tflops receives the FLOP/s
+ * (an FMA counts 2) in units of 1e12, *ms (if not NULL) the time of one
+ * launch.  Synchronises the stream; uses the cached workspace (1 float per
+ * thread of the launch).
+ */
+sp_status sp_fp32_peak(int32_t packed, double *tflops, float *ms, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,12 +6,14 @@ B-splines (degree 0-3) over any list of lines, and its exact adjoint
 the C ABI of include/spline_project.h; this package is a thin ctypes binding
 (`_lib`) plus the differentiable operator built on it.
 """
-from ._lib import (BASIS_BOX3, BASIS_BSPLINE, Batch, Grid, Lines, Plan, SplineError, load, sp_release_workspace, sp_version,
+from ._lib import (BASIS_BOX3, BASIS_BSPLINE, Batch, Grid, Lines, Plan, SplineError, fp32_peak, load,
+                   sp_release_workspace, sp_version,
                    spline_footprint_eval, spline_lines_expand, spline_project_adj,
                    spline_project_fwd, spline_visited)
 from .autograd import backproject, project
 
-__all__ = ["BASIS_BOX3", "BASIS_BSPLINE", "Batch", "Grid", "Lines", "Plan", "SplineError", "backproject", "load", "project",
+__all__ = ["BASIS_BOX3", "BASIS_BSPLINE", "Batch", "Grid", "Lines", "Plan", "SplineError", "backproject", "fp32_peak",
+           "load", "project",
            "sp_release_workspace", "sp_version",
            "spline_footprint_eval", "spline_lines_expand", "spline_project_adj",
            "spline_project_fwd", "spline_visited"]

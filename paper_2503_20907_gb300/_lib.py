@@ -43,7 +43,7 @@ class SplineError(RuntimeError):
 
 EXPORTED = ("sp_lines_count", "spline_project_fwd", "spline_project_adj", "spline_lines_expand",
             "spline_footprint_eval", "spline_visited", "sp_release_workspace", "sp_last_error",
-            "sp_version", "spline_plan_create", "spline_plan_prepare", "spline_plan_fwd",
+            "sp_version", "sp_fp32_peak", "spline_plan_create", "spline_plan_prepare", "spline_plan_fwd",
             "spline_plan_adj", "spline_plan_lines", "spline_plan_record_bytes", "spline_plan_set_records",
             "spline_plan_destroy",
             "spline_plan_stats",
@@ -130,6 +130,8 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
     lib.sp_release_workspace.argtypes = []
     lib.sp_last_error.restype = ctypes.c_char_p
     lib.sp_version.restype = ctypes.c_int32
+    lib.sp_fp32_peak.restype = st
+    lib.sp_fp32_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), P]
     _lib = lib
     return lib
 
@@ -288,6 +290,14 @@ def sp_release_workspace():
 
 def sp_version() -> int:
     return int(load().sp_version())
+
+
+def fp32_peak(packed: bool = False, stream=None) -> tuple[float, float]:
+    """Measured FP32 throughput of the current device (sp_fp32_peak): scalar
+    or packed (fma.rn.f32x2) FMA chains.  Returns (TFLOP/s, ms per launch)."""
+    t, ms = ctypes.c_double(0.0), ctypes.c_float(0.0)
+    _check(load().sp_fp32_peak(1 if packed else 0, ctypes.byref(t), ctypes.byref(ms), _stream(stream)))
+    return float(t.value), float(ms.value)
 
 
 class Plan:

@@ -1050,4 +1050,40 @@ const char *sp_last_error(void) { return g_err.c_str(); }
 
 int32_t sp_version(void) { return 100; }
 
+sp_status sp_fp32_peak(int32_t packed, double *tflops, float *ms, void *stream)
+{
+    g_err.clear();
+    if (packed != 0 && packed != 1) return fail(SP_EINVAL, "packed must be 0 or 1");
+    if (!tflops) return fail(SP_EINVAL, "tflops is NULL");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    const int blocks = 8 * sms, iters = 8192;   // 2048 threads per SM, ~10 ms
+    void *ws = nullptr;
+    sp_status st = workspace(sizeof(float) * 256 * (size_t)blocks, &ws);
+    if (st != SP_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 0.f;
+    if (e == cudaSuccess) e = spx::launch_fp32_peak(packed, blocks, iters, static_cast<float *>(ws), s);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = spx::launch_fp32_peak(packed, blocks, iters, static_cast<float *>(ws), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess && (k == 0 || t < best)) best = t;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "FP32 peak probe");
+    *tflops = (double)spx::fp32_peak_flops(packed, blocks, iters) / (1e-3 * (double)best) * 1e-12;
+    if (ms) *ms = best;
+    return SP_OK;
+}
+
 }  // extern "C"

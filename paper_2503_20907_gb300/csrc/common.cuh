@@ -137,25 +137,6 @@ __device__ __forceinline__ float row_start(const LineHdr &H, float inv_a, int r,
     return u0;
 }
 
-// row_start for a row given as fr = (float)(r - r_ref) (exact): the step count
-// is carried as a float too, so the row costs one float-to-int conversion
-// (of k, returned) instead of four.  Same u_0 as row_start.
-__device__ __forceinline__ float row_start_f(const LineHdr &H, float inv_a, float fr, int &k)
-{
-    const float V = __fmaf_rn(fr, H.rho_hi + H.rho_lo, H.U0);
-    float fk = ceilf(V * inv_a) - 1.0f;
-    auto u0_of = [&](float kk) {
-        float big = __fsub_rn(__fmul_rn(fr, H.rho_hi), __fmul_rn(kk, H.a_hi));
-        float small = __fmaf_rn(fr, H.rho_lo, __fmul_rn(-kk, H.a_lo));
-        return __fadd_rn(__fadd_rn(H.U0, small), big);
-    };
-    float u0 = u0_of(fk);
-    if (u0 <= 0.0f) { fk -= 1.0f; u0 = u0_of(fk); }
-    else if (u0 > H.a) { fk += 1.0f; u0 = u0_of(fk); }
-    k = (int)fk;
-    return u0;
-}
-
 // Degree 0 near an axis has footprint ramps of width b, which can be far
 // narrower than one float ulp of u.  For that degree u_0 is carried as an
 // unevaluated sum hi + lo.
@@ -355,6 +336,10 @@ cudaError_t launch_strip_queue(bool adj, const StripJob *jobs, int njobs, int64_
 cudaError_t launch_footprint_eval(const GridDev &g, int64_t count, const float *theta, const float *yt,
                                   float *out, float *scratch, cudaStream_t s);
 
+
+// FP32 throughput probe (peak.cu): FLOPs of one launch, and the launch.
+int64_t fp32_peak_flops(int packed, int blocks, int iters);
+cudaError_t launch_fp32_peak(int packed, int blocks, int iters, float *out, cudaStream_t s);
 
 // Argument errors and the thread-local message of the C ABI (api.cu), for the
 // entry points defined in other translation units.

@@ -1,8 +1,10 @@
-// Forward projection and adjoint for structured geometries (parallel and fan
-// beams) with coefficient strips in shared memory.
+// Forward projection and adjoint with coefficient strips in shared memory,
+// for parallel and fan beams and for free line lists sorted into the same
+// kind of chunks (order.cu).
 //
 // One CTA takes a chunk of up to kChunk neighbouring lines of one view
-// (consecutive detector bins).  Such lines are nearly parallel and adjacent,
+// (consecutive detector bins, or consecutive lines of a sorted free list).
+// Such lines are nearly parallel and adjacent,
 // so in every major-axis row their runs of nonzero nodes fall inside a short
 // window; the CTA keeps those windows (a skewed strip, one row per major-axis
 // row) in shared memory: staged from the coefficients for the forward
@@ -11,9 +13,10 @@
 // contiguous in global memory.
 //
 // One warp takes one line at a time, in batches of up to kBatch rows:
-//   A. lane per row: u_0, its interval sigma, t = u_0 - s_sigma and the strip
-//      offset of the row's first candidate; the rows are then ordered by
-//      sigma (counting sort, in the warp's shared memory);
+//   A. lane per row: u_0 (stepped from row to row in 64-bit fixed point),
+//      its interval sigma, t = u_0 - s_sigma and the strip offset of the
+//      row's first candidate; the rows are then ordered by sigma (counting
+//      sort, in the warp's shared memory);
 //   B. lane per (candidate i, row slot): for each interval sigma the lane
 //      holds the polynomial T[sigma][i] in registers and runs it over the
 //      rows of that interval, two rows per packed FP32 FMA (fma.rn.f32x2).
@@ -316,6 +319,29 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
     const int coloff = sgn * ci;
     f2 acc2 = 0ull;
     float acc_slow = 0.f;
+    // a run fits the strip row iff its first column oq satisfies
+    // oq_lo <= oq <= oq_lo + kPitch - K (the run spans oq .. oq + sgn (K - 1))
+    const int oq_lo = sgn > 0 ? 0 : K - 1;
+    const unsigned oq_span = (unsigned)(kPitch - K);
+    // Row stepping in fixed point (degree >= 1): W(r) = 2^32 u(r)/a - 1 as a
+    // 64-bit integer, u(r) = U0 + (r - r_ref) rho the offset of row r at
+    // column q_ref.  Its high word is the row's step count k (u_0 = u - k a
+    // in (0, a]) and u_0 = (low word + 1) a 2^-32.  rho/a and U0/a enter as
+    // float pairs (one correction step of the float quotient), rounded to 32
+    // fractional bits: over 2^11 rows that is within 2^-21 a of the exact u_0.
+    long long Wstep = 0, Wbase = 0;
+    float ua = 0.f;
+    if constexpr (DEG >= 1) {
+        auto fix_quot = [&](float xh, float xl) {
+            const float q1 = xh * inv_a;
+            const float r = __fmaf_rn(-q1, H.a_lo, __fmaf_rn(-q1, H.a_hi, xh) + xl);
+            const float q2 = r * inv_a;
+            return __float2ll_rn(q1 * 4294967296.f) + __float2ll_rn(q2 * 4294967296.f);
+        };
+        Wstep = fix_quot(H.rho_hi, H.rho_lo);
+        Wbase = fix_quot(H.U0, H.U0_lo) - 1 - (long long)H.r_ref * Wstep;
+        ua = H.a * 2.3283064365386963e-10f;   // a 2^-32
+    }
 
     const int dummy_pos = kSlabRows * kPitch + kDummy / 2;
     const int rb = max(H.r_begin, S0), re = min(H.r_end, S1);
@@ -344,10 +370,12 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
         float tv[kRowsPerLane];
         int pv[kRowsPerLane], sv[kRowsPerLane];
         unsigned long long own = 0ull;
-        const float fr0 = (float)(r0 + lane - H.r_ref);   // row offsets as exact floats
+        long long W = Wbase + (long long)(r0 + lane) * Wstep;   // W of this lane's first row
 #pragma unroll
         for (int j = 0; j < kRowsPerLane; ++j) {
             const int r = r0 + j * 32 + lane;
+            const long long Wr = W;
+            W += 32 * Wstep;
             sv[j] = -1;
             tv[j] = 0.f;
             pv[j] = 0;
@@ -356,9 +384,8 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
                 if constexpr (DEG == 0) {
                     e = row_eval<0>(H, s, inv_a, sgn, r);
                 } else {
-                    // as row_eval, with one float-to-int conversion per row
-                    int k;
-                    const float u0 = row_start_f(H, inv_a, fr0 + (float)(32 * j), k);
+                    const int k = (int)(Wr >> 32);
+                    const float u0 = __fmaf_rn((float)(unsigned)Wr, ua, ua);
                     float s_lo;
                     e.sg = sigma_of<DEG>(s, u0, s_lo);
                     e.t = u0 - s_lo;
@@ -366,9 +393,7 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
                 }
                 const int rr = r - S0;
                 const int oq = e.q0 - clo[rr];
-                const int lo = sgn > 0 ? oq : oq - (K - 1);
-                const int hi = sgn > 0 ? oq + (K - 1) : oq;
-                if (lo >= 0 && hi < kPitch) {
+                if ((unsigned)(oq - oq_lo) <= oq_span) {
                     sv[j] = e.sg;
                     tv[j] = e.t;
                     pv[j] = rr * kPitch + oq;

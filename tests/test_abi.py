@@ -73,6 +73,9 @@ def test_host_side_argument_checks(lib):
     gu = L.SpGrid(8, 8, 1, 5, 1.0, 0.0, 0.0)          # unknown basis
     assert lib.spline_project_fwd(ctypes.byref(gu), 1, ctypes.byref(fan), 1, None) == L.SP_EINVAL
     assert lib.sp_version() >= 100
+    t = ctypes.c_double(0.0)
+    assert lib.sp_fp32_peak(2, ctypes.byref(t), None, None) == L.SP_EINVAL   # packed must be 0 or 1
+    assert lib.sp_fp32_peak(0, None, None, None) == L.SP_EINVAL
 
 
 def test_plan_and_batch_host_side_checks(lib):
