@@ -47,9 +47,9 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kChunk = 32;          // lines per chunk
 constexpr int kPitch = 44;          // strip row length (floats), whole 16-byte chunks
 constexpr int kWin = kPitch - 3;    // window width that fits once its start is rounded down to 4 columns
-constexpr int kSlabRows = 408;      // strip rows held at once
+constexpr int kSlabRows = 360;      // strip rows held at once (one sorting batch per line and slab)
 constexpr int kDummy = 16;          // zero floats after the strip: target of padding records
-constexpr int kBatch = 256;         // rows of one line per sorting batch (8 per lane)
+constexpr int kBatch = 384;         // rows of one line per sorting batch (12 per lane), >= kSlabRows
 constexpr int kRowsPerLane = kBatch / 32;
 constexpr int kEntCap = kBatch + 4 * kMaxSig;   // sorted row records, segments padded to multiples of 4
 
@@ -69,6 +69,8 @@ static_assert(kTabBufBytes % 16 == 0 && kWarpBytes % 16 == 0 && kStripBytes % 16
               "16-byte alignment of the shared-memory regions");
 static_assert(kSmemBytes <= 115712, "two CTAs per SM");
 static_assert(kPitch % 4 == 0, "strip rows of whole 16-byte chunks");
+static_assert(kSlabRows * kPitch + kDummy < (1 << 16), "strip offsets fit 16 bits (phase A packs sigma above them)");
+static_assert(kBatch >= kSlabRows && kEntCap < 512, "one batch per line and slab; 9-bit counters of the sort");
 
 // ------------------------------------------------------------------ packed FP32
 typedef unsigned long long f2;
@@ -294,6 +296,31 @@ __device__ float strip_tie_line(const LineHdr &H, const float *tabw, int S0, int
 // strip.  tabw is the line's table in shared memory; ent_t / ent_p hold the
 // warp's sorted row records (t, strip offset of candidate 0).  FIX: the
 // adjoint's fixed-point strip (hpS = hp S); RM: the row-record mode.
+// A row whose run fell outside the staged window: its candidates straight
+// from (forward; returns the partial sum) or to (adjoint) global memory, and
+// counted.  Kept out of line: it runs only on geometries the windows do not
+// anticipate, and inlined into every unrolled row of phase A it only
+// lengthened the kernel.
+template <int DEG, bool ADJ>
+__device__ __noinline__ float strip_slow_row(const float *tabw, int sg, float t, int q0, int sgn, int K, float a_corr,
+                                             int r, int Nq, const float *__restrict__ src, float *dst, float hp,
+                                             int *err)
+{
+    atomicAdd(err, 1);
+    const float *T0 = tabw + tab_poly(sg, 0);
+    float acc = 0.f;
+    for (int i = 0; i < K; ++i) {
+        const int q = q0 + sgn * i;
+        if ((unsigned)q < (unsigned)Nq) {
+            const float ti = (DEG == 0) ? __fmaf_rn((float)i, a_corr, t) : t;
+            const float phi = horner<DEG>(T0 + i * kNC, ti);
+            if constexpr (ADJ) atomicAdd(dst + (size_t)r * Nq + q, hp * phi);
+            else acc = __fmaf_rn(__ldg(src + (size_t)r * Nq + q), phi, acc);
+        }
+    }
+    return acc;
+}
+
 template <int DEG, bool ADJ, bool FIX = false, int RM = kRecNone>
 __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, int *ent_p, float *strip, const int *clo,
                             int S0, int S1, int lane, const float *__restrict__ src, float *dst, int Nq,
@@ -311,7 +338,7 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
     for (int q = 0; q <= DEG; ++q) s[q] = tabw[q];
     const int K = H.K;
     // phase B lane roles: candidate ci of row slot sl (nsl slots of K lanes)
-    const int rk = (256 + K - 1) / K;   // (l * rk) >> 8 == l / K for l < 32, K <= 8
+    const int rk = (int)ceilf(256.0f * __frcp_rn((float)K));   // ceil(256 / K): (l * rk) >> 8 == l / K for l < 32, K <= 8   // (l * rk) >> 8 == l / K for l < 32, K <= 8
     const int nsl = (32 * rk) >> 8;
     const int sl = (lane * rk) >> 8;
     const int ci = lane - sl * K;
@@ -368,7 +395,7 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
         if (!ready) {
         // ---- A: lane per row
         float tv[kRowsPerLane];
-        int pv[kRowsPerLane], sv[kRowsPerLane];
+        int pv[kRowsPerLane];
         unsigned long long own = 0ull;
         long long W = Wbase + (long long)(r0 + lane) * Wstep;   // W of this lane's first row
 #pragma unroll
@@ -376,9 +403,8 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
             const int r = r0 + j * 32 + lane;
             const long long Wr = W;
             W += 32 * Wstep;
-            sv[j] = -1;
             tv[j] = 0.f;
-            pv[j] = 0;
+            pv[j] = -1;
             if (r < re) {
                 RowEval e;
                 if constexpr (DEG == 0) {
@@ -394,27 +420,16 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
                 const int rr = r - S0;
                 const int oq = e.q0 - clo[rr];
                 if ((unsigned)(oq - oq_lo) <= oq_span) {
-                    sv[j] = e.sg;
                     tv[j] = e.t;
-                    pv[j] = rr * kPitch + oq;
+                    pv[j] = (rr * kPitch + oq) | (e.sg << 16);
                     own += 1ull << (9 * e.sg);
                 } else if (rmode == kRecWrite) {
                     // the replay recomputes this batch (and reaches global memory then)
                     own |= kRecSlowBit;
                 } else {
                     // run outside the staged window: straight from or to global memory
-                    atomicAdd(err, 1);
-                    const float *T0 = tabw + tab_poly(e.sg, 0);
-                    for (int i = 0; i < K; ++i) {
-                        const int q = e.q0 + sgn * i;
-                        if ((unsigned)q < (unsigned)Nq) {
-                            // degree 0: candidate i sits i (|kappa| - a) further along u
-                            const float ti = (DEG == 0) ? __fmaf_rn((float)i, H.a_corr, e.t) : e.t;
-                            const float phi = horner<DEG>(T0 + i * kNC, ti);
-                            if constexpr (ADJ) atomicAdd(dst + (size_t)r * Nq + q, hp * phi);
-                            else acc_slow = __fmaf_rn(__ldg(src + (size_t)r * Nq + q), phi, acc_slow);
-                        }
-                    }
+                    acc_slow += strip_slow_row<DEG, ADJ>(tabw, e.sg, e.t, e.q0, sgn, K, H.a_corr, r, Nq, src, dst,
+                                                         hp, err);
                 }
             }
         }
@@ -446,12 +461,12 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
         unsigned long long cur = basep + (inc - own);
 #pragma unroll
         for (int j = 0; j < kRowsPerLane; ++j) {
-            if (sv[j] >= 0) {
-                const int sh = 9 * sv[j];
+            if (pv[j] >= 0) {
+                const int sh = 9 * (pv[j] >> 16);
                 const int idx = (int)((cur >> sh) & 511ull);
                 cur += 1ull << sh;
                 ent_t[idx] = tv[j];
-                ent_p[idx] = pv[j];
+                ent_p[idx] = pv[j] & 0xffff;
             }
         }
         __syncwarp();
