@@ -338,7 +338,7 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
     for (int q = 0; q <= DEG; ++q) s[q] = tabw[q];
     const int K = H.K;
     // phase B lane roles: candidate ci of row slot sl (nsl slots of K lanes)
-    const int rk = (int)ceilf(256.0f * __frcp_rn((float)K));   // ceil(256 / K): (l * rk) >> 8 == l / K for l < 32, K <= 8   // (l * rk) >> 8 == l / K for l < 32, K <= 8
+    const int rk = (int)ceilf(256.0f * __frcp_rn((float)K));   // ceil(256 / K): (l * rk) >> 8 == l / K for l < 32, K <= 8
     const int nsl = (32 * rk) >> 8;
     const int sl = (lane * rk) >> 8;
     const int ci = lane - sl * K;
