@@ -124,6 +124,8 @@ constexpr float kPhiBound = 1.5f;
 // and a flag for batches with runs outside the staged window, which the
 // replay recomputes), then t[R] and the strip offsets[R].
 enum RecMode { kRecNone = 0, kRecWrite = 1, kRecRead = 2 };
+// Which chunks an adjoint call runs (strip_chunk's FM).
+enum FixMode { kFmAll = 0, kFmFixed = 1, kFmFloat = 2 };
 constexpr unsigned long long kRecSlowBit = 1ull << 63;
 
 template <int NS>
@@ -526,7 +528,21 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
 // transposed image).
 // One chunk (view v, bins j0..j0+31) of one instance; smem is the CTA's
 // dynamic shared memory (kSmemBytes).
-template <int DEG, bool ADJ, int RM = kRecNone>
+template <int DEG, int RM>
+__device__ __noinline__ void strip_chunk_float_adj(unsigned char *smem, const GridDev g, const LinesDev L,
+                                                   const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
+                                                   float *__restrict__ sino, float *__restrict__ out,
+                                                   float *__restrict__ outT, int chunks_per_view, int vec, int *err,
+                                                   int chunk, unsigned char *rec, long long rec_cap);
+
+// FM (adjoint only) picks the chunks a call runs and their accumulators:
+// kFmAll runs every chunk, those that need float accumulators (see the top
+// of the file) through an out-of-line copy with float strips; kFmFixed runs
+// only the fixed-point chunks and kFmFloat only the others, so that a
+// launch of each covers every chunk and the fixed-point kernel carries no
+// second copy of the line code (a second inlined copy, or a call anywhere in
+// the kernel, made the fixed-point adjoint about a tenth slower).
+template <int DEG, bool ADJ, int RM = kRecNone, int FM = kFmAll>
 __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g, const LinesDev L,
                                             const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
                                             const float *__restrict__ coef, const float *__restrict__ coefT,
@@ -563,24 +579,6 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
     const int64_t line0 = (int64_t)v * nd + j0;
     const int my_line = lane < nl ? (L.order ? __ldg(L.order + line0 + lane) : (int)(line0 + lane)) : 0;
 
-    if (!ADJ && threadIdx.x < kChunk) line_acc[threadIdx.x] = 0.f;
-    if (threadIdx.x < kChunk) rec_off[threadIdx.x] = 0;
-    if (!ADJ && threadIdx.x < kDummy) strip[kSlabRows * kPitch + threadIdx.x] = 0.f;
-    // the chunk's line records into shared memory, its tables towards L2
-    // (lines other than parallel beams have one table each, indexed by line)
-    static_assert(kChunk * 4 <= kThreads, "one pass over the chunk's line records");
-    {
-        const int src = __shfl_sync(0xffffffffu, my_line, (threadIdx.x >> 2) & 31);
-        if ((int)threadIdx.x < nl * 4)
-            reinterpret_cast<int4 *>(hdr_s)[threadIdx.x] =
-                __ldg(reinterpret_cast<const int4 *>(hdr + src) + (threadIdx.x & 3));
-    }
-    if (L.kind != SP_LINES_PARALLEL)
-        for (int i0 = 0; i0 < kChunk * kTabLines; i0 += kThreads) {
-            const int i = i0 + threadIdx.x;
-            const int src = __shfl_sync(0xffffffffu, my_line, min(i / kTabLines, kChunk - 1));
-            if (i < nl * kTabLines) prefetch_l2(tabs + (int64_t)src * kTabFloats + (i % kTabLines) * 32);
-        }
     if constexpr (ADJ) {
         // The chunk's fixed-point scale S (a power of two; see the top of the
         // file): misc[5] = 1 if the strip accumulates in fixed point, misc[6]
@@ -606,14 +604,46 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                 misc[7] = __float_as_int(ldexpf(1.f, -e));
             }
         }
+        __syncthreads();
+        const bool fx = misc[5] != 0;
+        if constexpr (FM == kFmFixed) {
+            if (!fx) return;   // left to the float launch
+        } else if constexpr (FM == kFmFloat) {
+            if (fx) return;    // done by the fixed-point launch
+        } else {
+            if (!fx) {
+                __syncthreads();
+                strip_chunk_float_adj<DEG, RM>(smem, g, L, hdr, tabs, sino, out, outT, chunks_per_view, vec, err,
+                                               chunk, rec, rec_cap);
+                return;
+            }
+        }
     }
 
+    if (!ADJ && threadIdx.x < kChunk) line_acc[threadIdx.x] = 0.f;
+    if (threadIdx.x < kChunk) rec_off[threadIdx.x] = 0;
+    if (!ADJ && threadIdx.x < kDummy) strip[kSlabRows * kPitch + threadIdx.x] = 0.f;
+    // the chunk's line records into shared memory, its tables towards L2
+    // (lines other than parallel beams have one table each, indexed by line)
+    static_assert(kChunk * 4 <= kThreads, "one pass over the chunk's line records");
+    {
+        const int src = __shfl_sync(0xffffffffu, my_line, (threadIdx.x >> 2) & 31);
+        if ((int)threadIdx.x < nl * 4)
+            reinterpret_cast<int4 *>(hdr_s)[threadIdx.x] =
+                __ldg(reinterpret_cast<const int4 *>(hdr + src) + (threadIdx.x & 3));
+    }
+    if (L.kind != SP_LINES_PARALLEL)
+        for (int i0 = 0; i0 < kChunk * kTabLines; i0 += kThreads) {
+            const int i = i0 + threadIdx.x;
+            const int src = __shfl_sync(0xffffffffu, my_line, min(i / kTabLines, kChunk - 1));
+            if (i < nl * kTabLines) prefetch_l2(tabs + (int64_t)src * kTabFloats + (i % kTabLines) * 32);
+        }
     bool fixed = false;
     float fscale = 1.f, finv = 1.f;
     for (int axis = 0; axis < 2; ++axis) {
         __syncthreads();
         if (ADJ && axis == 0) {
-            fixed = misc[5] != 0;
+            fixed = FM != kFmFloat && misc[5] != 0;
             fscale = __int_as_float(misc[6]);
             finv = __int_as_float(misc[7]);
         }
@@ -811,14 +841,16 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
                     unsigned char *rp = lrec ? lrec + rec_off[li] : nullptr;
                     const unsigned char *rend = lrec ? lrec + rec_cap : nullptr;
                     float part;
-                    if (ADJ && fixed)
-                        part = strip_line<DEG, ADJ, true, RM>(H, tabbuf + buf * kTabFloats, ent_t, ent_p, strip,
-                                                                      clo, S0, S1, lane, src, dst, Nq, err, hp,
-                                                                      hp * fscale, rp, rend);
-                    else
-                        part = strip_line<DEG, ADJ, false, RM>(H, tabbuf + buf * kTabFloats, ent_t, ent_p,
-                                                                       strip, clo, S0, S1, lane, src, dst, Nq, err, hp,
-                                                                       0.f, rp, rend);
+                    if constexpr (ADJ) {
+                        part = strip_line<DEG, true, FM != kFmFloat, RM>(H, tabbuf + buf * kTabFloats, ent_t, ent_p,
+                                                                         strip, clo, S0, S1, lane, src, dst, Nq, err,
+                                                                         hp, FM != kFmFloat ? hp * fscale : 0.f, rp,
+                                                                         rend);
+                    } else {
+                        part = strip_line<DEG, false, false, RM>(H, tabbuf + buf * kTabFloats, ent_t, ent_p, strip,
+                                                                 clo, S0, S1, lane, src, dst, Nq, err, hp, 0.f, rp,
+                                                                 rend);
+                    }
                     if (!ADJ && rmode != kRecWrite) {
                         const float sum = warp_sum(part);
                         if (lane == 0) line_acc[li] += sum;
@@ -872,7 +904,21 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
     }
 }
 
-template <int DEG, bool ADJ, int RM>
+template <int DEG, int RM>
+__device__ __noinline__ void strip_chunk_float_adj(unsigned char *smem, const GridDev g, const LinesDev L,
+                                                   const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
+                                                   float *__restrict__ sino, float *__restrict__ out,
+                                                   float *__restrict__ outT, int chunks_per_view, int vec, int *err,
+                                                   int chunk, unsigned char *rec, long long rec_cap)
+{
+    strip_chunk<DEG, true, RM, kFmFloat>(smem, g, L, hdr, tabs, nullptr, nullptr, sino, out, outT, chunks_per_view,
+                                         vec, err, chunk, rec, rec_cap);
+}
+
+// One CTA per chunk.  The adjoint runs as two launches over all chunks: FM
+// kFmFixed (the fixed-point chunks, nearly all) and then kFmFloat (the rest;
+// its CTAs return after one look at their chunk's sinogram values).
+template <int DEG, bool ADJ, int RM, int FM = kFmAll>
 __global__ void __launch_bounds__(kThreads, 2)
 strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
              const float *__restrict__ coef, const float *__restrict__ coefT, float *__restrict__ sino,
@@ -880,8 +926,8 @@ strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float
              unsigned char *rec, long long rec_cap)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    strip_chunk<DEG, ADJ, RM>(smem, g, L, hdr, tabs, coef, coefT, sino, out, outT, chunks_per_view, vec, err,
-                                   (int)blockIdx.x, rec, rec_cap);
+    strip_chunk<DEG, ADJ, RM, FM>(smem, g, L, hdr, tabs, coef, coefT, sino, out, outT, chunks_per_view, vec, err,
+                                  (int)blockIdx.x, rec, rec_cap);
 }
 
 // Persistent kernel over the chunks of several instances: each CTA takes the
@@ -975,10 +1021,16 @@ cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *h
         if (e == cudaSuccess) e = cudaMemsetAsync(imgT, 0, sizeof(float) * (size_t)g.nx * g.ny, s);
         if (e != cudaSuccess) return e;
     }
-    auto kern = rmode == kRecRead ? strip_kernel<DEG, ADJ, kRecRead>
-                : rmode == kRecWrite ? strip_kernel<DEG, ADJ, (ADJ ? kRecNone : kRecWrite)>
-                                     : strip_kernel<DEG, ADJ, kRecNone>;
+    // the adjoint: fixed-point chunks, then (a second launch) float chunks
+    constexpr int FM1 = ADJ ? kFmFixed : kFmAll;
+    auto kern = rmode == kRecRead ? strip_kernel<DEG, ADJ, kRecRead, FM1>
+                : rmode == kRecWrite ? strip_kernel<DEG, ADJ, (ADJ ? kRecNone : kRecWrite), FM1>
+                                     : strip_kernel<DEG, ADJ, kRecNone, FM1>;
+    auto kern2 = rmode == kRecRead ? strip_kernel<DEG, ADJ, kRecRead, kFmFloat>
+                                   : strip_kernel<DEG, ADJ, kRecNone, kFmFloat>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e == cudaSuccess && ADJ)
+        e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     if (strip_needs_order(L) && !L.order) return cudaErrorInvalidValue;   // free lists need their order
     const int cpv = (int)((chunk_bins(L) + kChunk - 1) / kChunk);
@@ -990,6 +1042,11 @@ cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *h
     kern<<<grid, kThreads, kSmemBytes, s>>>(g, L, hdr, tabs, coef, imgT, const_cast<float *>(sino), out, imgT, cpv,
                                             vec, err, rb, rcap);
     e = cudaGetLastError();
+    if (e == cudaSuccess && ADJ) {
+        kern2<<<grid, kThreads, kSmemBytes, s>>>(g, L, hdr, tabs, coef, imgT, const_cast<float *>(sino), out, imgT,
+                                                 cpv, vec, err, rb, rcap);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess && ADJ && rmode != kRecWrite) {
         add_transposed_kernel<<<tg, tb, 0, s>>>(imgT, out, g.nx, g.ny);
         e = cudaGetLastError();

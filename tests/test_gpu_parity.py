@@ -298,3 +298,50 @@ def test_diagonal_and_axis_lines_through_nodes(n):
     lines = sp.Lines.theta_y(torch.from_numpy(th).to(DEV), torch.from_numpy(y).to(DEV))
     sino = sp.spline_project_fwd(g, torch.from_numpy(coef).to(DEV), lines).cpu().numpy()
     assert rel_l2(sino, oracle.forward(og, coef, th.astype(np.float64), y.astype(np.float64))) < TOL
+
+
+@pytest.mark.parametrize("records", [False, True])
+def test_adjoint_float_strips_for_extreme_and_nonfinite_values(records):
+    # A chunk whose sinogram values are too large or too small for its
+    # fixed-point scale, or not finite, accumulates its strip in FP32 (an
+    # out-of-line copy of the strip adjoint): views of values ~1e25 and
+    # ~1e-25 beside ordinary ones, against the warp-per-line adjoint and the
+    # oracle; a NaN reaches exactly the nodes its line touches.
+    W = workloads.crop_workload(workloads.workload("fan512_cubic"), 64, seed=13)
+    g, og = _grid(W.n, W.degree, W.h)
+    lines = device_lines(W.geometry, DEV)
+    nd = W.geometry.n_det
+    rng = np.random.default_rng(8)
+    p = rng.uniform(0.5, 1.5, lines.m)
+    p[:nd] *= 1e25
+    p[nd:2 * nd] *= 1e-25
+    p = p.astype(np.float32)
+    plan = sp.Plan(g, lines, prepare=True, records=records)
+    back = plan.adj(torch.from_numpy(p).to(DEV)).clone()
+    plan.set_paths(0, 2)
+    ref = plan.adj(torch.from_numpy(p).to(DEV))
+    torch.cuda.synchronize()
+    assert float((back - ref).double().norm() / ref.double().norm()) < 1e-6
+    th, yy = oracle_lines(W.geometry)
+    assert rel_l2(back.cpu().numpy(), oracle.adjoint(og, p.astype(np.float64), th, yy)) < TOL
+    # the second view alone (tiny values) against the oracle, to its own scale
+    q = np.zeros_like(p)
+    q[nd:2 * nd] = p[nd:2 * nd]
+    plan.set_paths(0, 0)
+    small = plan.adj(torch.from_numpy(q).to(DEV)).cpu().numpy()
+    assert rel_l2(small, oracle.adjoint(og, q.astype(np.float64), th, yy)) < TOL
+    # a NaN reaches every node the line's footprint covers, and nothing
+    # farther than the neighbours of those (the row's candidate slots at the
+    # ends of its run, where the footprint is 0, get NaN * 0 too)
+    r = np.ones_like(p)
+    r[3 * nd + 100] = np.nan
+    got = np.isnan(plan.adj(torch.from_numpy(r).to(DEV)).cpu().numpy())
+    mask = np.zeros(lines.m)
+    mask[3 * nd + 100] = 1.0
+    touched = oracle.adjoint(og, mask, th, yy) != 0.0
+    assert touched.any() and np.all(got[touched])
+    near = np.pad(touched, 1)
+    near = np.logical_or.reduce([near[1 + di:near.shape[0] - 1 + di, 1 + dj:near.shape[1] - 1 + dj]
+                                 for di in (-1, 0, 1) for dj in (-1, 0, 1)])
+    assert not np.any(got & ~near)
+    plan.close()
