@@ -34,7 +34,7 @@ METRIC = "Mrays/s fwd+adj at 512² cubic fan-beam (% roofline); learned-vs-cold 
 UNIT = "Mrays/s"
 WORKLOAD = "fan512_cubic"
 FP32_LANES_PER_SM = 128
-KERNELS_PER_STEP = 5   # line setup with tables (one fused kernel), transpose + forward strip, adjoint strip + transposed add
+KERNELS_PER_STEP = 6   # line setup with tables (one fused kernel), transpose + forward strip, adjoint strip (fixed-point chunks, then float chunks) + transposed add
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
 # capture of these kernel versions on this workload); set to None whenever the
 # kernels change until they are captured again.

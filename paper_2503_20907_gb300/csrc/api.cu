@@ -682,7 +682,13 @@ struct sp_batch {
     spx::StripJob *jobs_dev[2] = {nullptr, nullptr};   // forward, adjoint
     std::vector<spx::StripJob> jobs_host[2];
     int64_t chunks[2] = {0, 0};
-    unsigned long long *counter = nullptr;              // [2]
+    // jobs grouped by kernel degree (one queue launch per degree):
+    // jobs [gjob0, gjob0 + gnjob) of group deg own gtotal chunks
+    int gjob0[2][4] = {}, gnjob[2][4] = {};
+    int64_t gtotal[2][4] = {};
+    unsigned long long *counter = nullptr;              // [2][3 degrees][3]: queue counters
+    long long *defer = nullptr;                          // adjoint chunks deferred to float strips
+    int64_t defer_cap = 0;
 };
 
 }  // extern "C"
@@ -702,6 +708,7 @@ void batch_free(sp_batch *b)
     for (int d = 0; d < 2; ++d)
         if (b->jobs_dev[d]) cudaFree(b->jobs_dev[d]);
     if (b->counter) cudaFree(b->counter);
+    if (b->defer) cudaFree(b->defer);
     for (sp_plan *p : b->plans) spline_plan_destroy(p);
     delete b;
 }
@@ -760,26 +767,41 @@ cudaError_t upload_jobs(sp_batch *b, int d, In in, Out outp, std::vector<char> &
 {
     std::vector<spx::StripJob> &hj = b->jobs_host[d];
     hj.clear();
-    int64_t c0 = 0;
     queued.assign(b->plans.size(), 0);
-    for (size_t i = 0; i < b->plans.size(); ++i) {
-        const sp_plan *p = b->plans[i];
-        const int path = d ? p->path_adj : p->path_fwd;
-        // degree 0 (strip kernels only when set or tuned) keeps its own launch:
-        // the queue kernel carries degrees 1-3
-        if (p->L.m == 0 || p->g.kdeg < 1 || !use_strip(p->g, p->L, p->extra, path)) continue;
-        spx::StripJob J = d ? spx::make_strip_job(p->g, p->L, p->hdr, p->tabs, true, nullptr,
-                                                  const_cast<float *>(in[i]), outp[i], p->extra,
-                                                  slow_counter(p->g, p->extra))
-                            : spx::make_strip_job(p->g, p->L, p->hdr, p->tabs, false, in[i], outp[i], nullptr,
-                                                  p->extra, slow_counter(p->g, p->extra));
-        J.chunk0 = c0;
-        c0 += spx::strip_job_chunks(J);
-        hj.push_back(J);
-        queued[i] = 1;
+    int64_t all = 0;
+    for (int deg = 1; deg <= 3; ++deg) {
+        b->gjob0[d][deg] = (int)hj.size();
+        int64_t c0 = 0;   // chunk indices count within the degree's group
+        for (size_t i = 0; i < b->plans.size(); ++i) {
+            const sp_plan *p = b->plans[i];
+            const int path = d ? p->path_adj : p->path_fwd;
+            // degree 0 (strip kernels only when set or tuned) keeps its own
+            // launch: the queue kernels carry degrees 1-3
+            if (p->g.kdeg != deg || p->L.m == 0 || !use_strip(p->g, p->L, p->extra, path)) continue;
+            spx::StripJob J = d ? spx::make_strip_job(p->g, p->L, p->hdr, p->tabs, true, nullptr,
+                                                      const_cast<float *>(in[i]), outp[i], p->extra,
+                                                      slow_counter(p->g, p->extra))
+                                : spx::make_strip_job(p->g, p->L, p->hdr, p->tabs, false, in[i], outp[i], nullptr,
+                                                      p->extra, slow_counter(p->g, p->extra));
+            J.chunk0 = c0;
+            c0 += spx::strip_job_chunks(J);
+            hj.push_back(J);
+            queued[i] = 1;
+        }
+        b->gnjob[d][deg] = (int)hj.size() - b->gjob0[d][deg];
+        b->gtotal[d][deg] = c0;
+        all += c0;
     }
+    const int64_t c0 = all;
     b->chunks[d] = c0;
     cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && d == 1 && c0 > b->defer_cap) {
+        if (b->defer) cudaFree(b->defer);
+        b->defer = nullptr;
+        b->defer_cap = 0;
+        e = cudaMalloc(&b->defer, sizeof(long long) * (size_t)c0);
+        if (e == cudaSuccess) b->defer_cap = c0;
+    }
     if (e == cudaSuccess && !hj.empty())
         e = cudaMemcpy(b->jobs_dev[d], hj.data(), sizeof(spx::StripJob) * hj.size(), cudaMemcpyHostToDevice);
     return e;
@@ -792,8 +814,14 @@ cudaError_t run_queue(sp_batch *b, int d, cudaStream_t s)
     const std::vector<spx::StripJob> &hj = b->jobs_host[d];
     cudaError_t e = cudaSuccess;
     for (size_t k = 0; k < hj.size() && e == cudaSuccess; ++k) e = spx::launch_strip_pre(hj[k], d == 1, s);
-    if (e == cudaSuccess)
-        e = spx::launch_strip_queue(d == 1, b->jobs_dev[d], (int)hj.size(), b->chunks[d], b->counter + d, s);
+    int64_t defer0 = 0;   // each degree's deferred chunks in its own part of the list
+    for (int deg = 1; deg <= 3 && e == cudaSuccess; ++deg) {
+        if (b->gnjob[d][deg] == 0) continue;
+        e = spx::launch_strip_queue(deg, d == 1, b->jobs_dev[d] + b->gjob0[d][deg], b->gnjob[d][deg],
+                                    b->gtotal[d][deg], b->counter + 9 * d + 3 * (deg - 1),
+                                    d == 1 ? b->defer + defer0 : nullptr, s);
+        defer0 += b->gtotal[d][deg];
+    }
     for (size_t k = 0; k < hj.size() && e == cudaSuccess; ++k) e = spx::launch_strip_post(hj[k], d == 1, s);
     return e;
 }
@@ -822,7 +850,7 @@ sp_status spline_batch_create(int32_t count, const sp_grid *grids, const sp_line
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     for (int d = 0; d < 2 && e == cudaSuccess; ++d) e = cudaMalloc(&b->jobs_dev[d], sizeof(spx::StripJob) * (size_t)count);
-    if (e == cudaSuccess) e = cudaMalloc(&b->counter, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->counter, 18 * sizeof(unsigned long long));
     for (int k = 0; k < kBatchStreams && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);

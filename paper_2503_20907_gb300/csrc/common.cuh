@@ -330,9 +330,12 @@ int64_t strip_job_chunks(const StripJob &J);
 cudaError_t launch_strip_pre(const StripJob &J, bool adj, cudaStream_t s);
 cudaError_t launch_strip_post(const StripJob &J, bool adj, cudaStream_t s);
 // The persistent kernel over jobs[0..njobs) (device array, chunk0 ascending,
-// `total` chunks in all); counter is one device word, reset here.
-cudaError_t launch_strip_queue(bool adj, const StripJob *jobs, int njobs, int64_t total,
-                               unsigned long long *counter, cudaStream_t s);
+// `total` chunks in all, every job of kernel degree deg in 1..3); counter is
+// three device words, reset here.  The adjoint defers chunks that need float
+// strips to `defer` (device, room for `total` chunk indices) and runs them in
+// a second launch.
+cudaError_t launch_strip_queue(int deg, bool adj, const StripJob *jobs, int njobs, int64_t total,
+                               unsigned long long *counter, long long *defer, cudaStream_t s);
 cudaError_t launch_footprint_eval(const GridDev &g, int64_t count, const float *theta, const float *yt,
                                   float *out, float *scratch, cudaStream_t s);
 

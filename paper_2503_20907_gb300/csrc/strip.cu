@@ -543,7 +543,7 @@ __device__ __noinline__ void strip_chunk_float_adj(unsigned char *smem, const Gr
 // second copy of the line code (a second inlined copy, or a call anywhere in
 // the kernel, made the fixed-point adjoint about a tenth slower).
 template <int DEG, bool ADJ, int RM = kRecNone, int FM = kFmAll>
-__device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g, const LinesDev L,
+__device__ __forceinline__ bool strip_chunk(unsigned char *smem, const GridDev g, const LinesDev L,
                                             const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
                                             const float *__restrict__ coef, const float *__restrict__ coefT,
                                             float *__restrict__ sino, float *__restrict__ out,
@@ -607,15 +607,15 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
         __syncthreads();
         const bool fx = misc[5] != 0;
         if constexpr (FM == kFmFixed) {
-            if (!fx) return;   // left to the float launch
+            if (!fx) return false;   // left to the float launch
         } else if constexpr (FM == kFmFloat) {
-            if (fx) return;    // done by the fixed-point launch
+            if (fx) return false;    // done by the fixed-point launch
         } else {
             if (!fx) {
                 __syncthreads();
                 strip_chunk_float_adj<DEG, RM>(smem, g, L, hdr, tabs, sino, out, outT, chunks_per_view, vec, err,
                                                chunk, rec, rec_cap);
-                return;
+                return true;
             }
         }
     }
@@ -902,6 +902,7 @@ __device__ __forceinline__ void strip_chunk(unsigned char *smem, const GridDev g
         __syncthreads();
         if ((int)threadIdx.x < nl) sino[my_line] = g.h * line_acc[threadIdx.x];   // warp 0: lane = line
     }
+    return true;
 }
 
 template <int DEG, int RM>
@@ -930,13 +931,29 @@ strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float
                                   (int)blockIdx.x, rec, rec_cap);
 }
 
-// Persistent kernel over the chunks of several instances: each CTA takes the
-// next chunk from one counter (atomicAdd; no CTA waits on another) and runs it
-// with its instance's parameters, until every chunk is taken.  Instance k
-// owns chunks [jobs[k].chunk0, jobs[k + 1].chunk0).
-template <bool ADJ>
+// Persistent kernel over the chunks of several instances of one degree: each
+// CTA takes the next chunk from one counter (atomicAdd; no CTA waits on
+// another) and runs it with its instance's parameters, until every chunk is
+// taken.  Instance k owns chunks [jobs[k].chunk0, jobs[k + 1].chunk0).  The
+// adjoint runs the fixed-point chunks and appends the others to defer[]
+// (count *defer_n) for strip_queue_float_kernel, as the per-instance adjoint
+// does with its second launch.  (One kernel per degree: a kernel holding all
+// three degrees spilled over a hundred bytes per thread.)
+__device__ __forceinline__ const StripJob *queue_job(const StripJob *__restrict__ jobs, int njobs, long long c)
+{
+    int lo = 0, hi = njobs - 1;   // last job whose first chunk is <= c
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].chunk0 <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return jobs + lo;
+}
+
+template <int DEG, bool ADJ>
 __global__ void __launch_bounds__(kThreads, 2)
-strip_queue_kernel(const StripJob *__restrict__ jobs, int njobs, long long total, unsigned long long *counter)
+strip_queue_kernel(const StripJob *__restrict__ jobs, int njobs, long long total, unsigned long long *counter,
+                   long long *defer, unsigned long long *defer_n)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long cur;
@@ -946,29 +963,63 @@ strip_queue_kernel(const StripJob *__restrict__ jobs, int njobs, long long total
         __syncthreads();
         const long long c = cur;
         if (c >= total) break;
-        int lo = 0, hi = njobs - 1;   // last job whose first chunk is <= c
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].chunk0 <= c) lo = mid;
-            else hi = mid - 1;
-        }
-        const StripJob *J = jobs + lo;
-        const int local = (int)(c - J->chunk0);
-        switch (J->g.kdeg) {
-        case 1:
-            strip_chunk<1, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
-                                J->cpv, J->vec, J->err, local);
-            break;
-        case 2:
-            strip_chunk<2, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
-                                J->cpv, J->vec, J->err, local);
-            break;
-        default:
-            strip_chunk<3, ADJ>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT,
-                                J->cpv, J->vec, J->err, local);
-            break;
-        }
+        const StripJob *J = queue_job(jobs, njobs, c);
+        const bool ran = strip_chunk<DEG, ADJ, kRecNone, ADJ ? kFmFixed : kFmAll>(
+            smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino, J->out, J->outT, J->cpv, J->vec, J->err,
+            (int)(c - J->chunk0));
+        if (ADJ && !ran && threadIdx.x == 0) defer[atomicAdd(defer_n, 1ull)] = c;
     }
+}
+
+// The deferred adjoint chunks (float strip accumulators), persistent likewise.
+template <int DEG>
+__global__ void __launch_bounds__(kThreads, 2)
+strip_queue_float_kernel(const StripJob *__restrict__ jobs, int njobs, const long long *__restrict__ defer,
+                         const unsigned long long *__restrict__ defer_n, unsigned long long *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long cur;
+    const unsigned long long n = *defer_n;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) cur = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long k = cur;
+        if (k >= (long long)n) break;
+        const long long c = defer[k];
+        const StripJob *J = queue_job(jobs, njobs, c);
+        strip_chunk<DEG, true, kRecNone, kFmFloat>(smem, J->g, J->L, J->hdr, J->tabs, J->coef, J->coefT, J->sino,
+                                                   J->out, J->outT, J->cpv, J->vec, J->err, (int)(c - J->chunk0));
+    }
+}
+
+template <int DEG>
+cudaError_t launch_queue_t(bool adj, const StripJob *jobs, int njobs, int64_t total, unsigned long long *counter,
+                           long long *defer, int64_t grid, int sms, cudaStream_t s)
+{
+    cudaError_t e;
+    if (adj) {
+        e = cudaFuncSetAttribute(strip_queue_kernel<DEG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(strip_queue_float_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        strip_queue_kernel<DEG, true><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(jobs, njobs, (long long)total,
+                                                                                  counter, defer, counter + 1);
+        e = cudaGetLastError();
+        // the deferred chunks are few (non-finite or extreme sinogram values): a small grid
+        if (e == cudaSuccess)
+            strip_queue_float_kernel<DEG><<<(unsigned)(grid < sms ? grid : sms), kThreads, kSmemBytes, s>>>(
+                jobs, njobs, defer, counter + 1, counter + 2);
+        return e == cudaSuccess ? cudaGetLastError() : e;
+    }
+    e = cudaFuncSetAttribute(strip_queue_kernel<DEG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    strip_queue_kernel<DEG, false><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(jobs, njobs, (long long)total, counter,
+                                                                               nullptr, nullptr);
+    return cudaGetLastError();
 }
 
 __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int nx, int ny)
@@ -1100,27 +1151,23 @@ cudaError_t launch_strip_post(const StripJob &J, bool adj, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_strip_queue(bool adj, const StripJob *jobs, int njobs, int64_t total,
-                               unsigned long long *counter, cudaStream_t s)
+cudaError_t launch_strip_queue(int deg, bool adj, const StripJob *jobs, int njobs, int64_t total,
+                               unsigned long long *counter, long long *defer, cudaStream_t s)
 {
     if (njobs <= 0 || total <= 0) return cudaSuccess;
+    if (deg < 1 || deg > 3 || (adj && !defer)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     int64_t grid = 2 * (int64_t)sms;   // two CTAs per SM, resident at once
     if (grid > total) grid = total;
-    if (adj) {
-        e = cudaFuncSetAttribute(strip_queue_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-        if (e == cudaSuccess)
-            strip_queue_kernel<true><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(jobs, njobs, (long long)total, counter);
-    } else {
-        e = cudaFuncSetAttribute(strip_queue_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-        if (e == cudaSuccess)
-            strip_queue_kernel<false><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(jobs, njobs, (long long)total, counter);
+    switch (deg) {
+    case 1: return launch_queue_t<1>(adj, jobs, njobs, total, counter, defer, grid, sms, s);
+    case 2: return launch_queue_t<2>(adj, jobs, njobs, total, counter, defer, grid, sms, s);
+    default: return launch_queue_t<3>(adj, jobs, njobs, total, counter, defer, grid, sms, s);
     }
-    return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 bool strip_supported(const GridDev &g, const LinesDev &L)

@@ -159,3 +159,32 @@ def test_batch_queue_edge_cases():
 def test_batch_invalid():
     with pytest.raises(sp.SplineError):
         sp.Batch([sp.Grid(8, 8, 5)], [sp.Lines.theta_y(torch.zeros(3, device=DEV), torch.zeros(3, device=DEV))])
+
+
+def test_batch_defers_chunks_that_need_float_strips():
+    # sinogram values too large for a chunk's fixed-point scale, and a NaN:
+    # the queue kernel defers those chunks to its float launch; the results
+    # are the instances' own adjoints
+    grids, lines = _mixed_instances()
+    keep = [0, 1, 4]
+    grids, lines = [grids[k] for k in keep], [lines[k] for k in keep]
+    batch = sp.Batch(grids, lines)
+    plans = [sp.Plan(g, L) for g, L in zip(grids, lines)]
+    gen = torch.Generator(device="cpu").manual_seed(12)
+    sinos = [torch.rand(L.m, generator=gen).to(DEV) + 0.5 for L in lines]
+    sinos[1][:71] *= 1e25
+    sinos[2][:40] *= 1e-25
+    backs = batch.adj(sinos)
+    assert batch.queued(True) == 3
+    for b, p, s in zip(backs, plans, sinos):
+        ref = p.adj(s)
+        assert float((b - ref).double().norm() / ref.double().norm()) < 1e-6
+    nan = [s.clone() for s in sinos]
+    nan[0][2] = float("nan")
+    backs = batch.adj(nan)
+    for b, p, s in zip(backs, plans, nan):
+        ref = p.adj(s)
+        assert torch.equal(torch.isnan(b), torch.isnan(ref))
+        ok = ~torch.isnan(ref)
+        assert float((b[ok] - ref[ok]).double().norm() / ref[ok].double().norm()) < 1e-6
+    batch.close()
