@@ -142,16 +142,25 @@ size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 // Line records and footprint tables for (grid, lines) in the workspace.
 // Scratch of the strip kernels: transposed coefficients, the slow-row
 // counter, then (free line lists) the chunk order and its sort's scratch.
+size_t order_bytes(const spx::LinesDev &L) { return spx::strip_needs_order(L) ? align_up(spx::line_order_bytes(L.m)) : 0; }
+
 size_t extra_bytes(const spx::GridDev &g, const spx::LinesDev &L)
 {
     if (!spx::strip_supported(g, L)) return 0;
-    return align_up(spx::strip_scratch_bytes(g)) + 256 +
-           (spx::strip_needs_order(L) ? spx::line_order_bytes(L.m) : 0);
+    return align_up(spx::strip_scratch_bytes(g)) + 256 + order_bytes(L) +
+           sizeof(unsigned) * (size_t)(2 + spx::strip_chunk_count(L));
 }
 
 int *slow_counter(const spx::GridDev &g, void *extra)
 {
     return reinterpret_cast<int *>(static_cast<char *>(extra) + align_up(spx::strip_scratch_bytes(g)));
+}
+
+// The adjoint's list of chunks deferred to float strips (after the order).
+unsigned *defer_area(const spx::GridDev &g, const spx::LinesDev &L, void *extra)
+{
+    return reinterpret_cast<unsigned *>(static_cast<char *>(extra) + align_up(spx::strip_scratch_bytes(g)) + 256 +
+                                        order_bytes(L));
 }
 
 // Where the chunk order of a free line list lives (NULL for other kinds).
@@ -191,7 +200,8 @@ cudaError_t run_adj(const spx::GridDev &g, const spx::LinesDev &L, const spx::Li
     if (path == kPathGather && spx::gather_supported(g, L))
         return spx::launch_adj_gather(g, L, hdr, tabs, sino, coef_out, s);
     if (use_strip(g, L, extra, path))
-        return spx::launch_adj_strip(g, L, hdr, tabs, sino, extra, coef_out, slow_counter(g, extra), s, rec);
+        return spx::launch_adj_strip(g, L, hdr, tabs, sino, extra, coef_out, slow_counter(g, extra), s, rec,
+                                     defer_area(g, L, extra));
     return spx::launch_adj(g, hdr, tabs, L.m, sino, coef_out, s);
 }
 

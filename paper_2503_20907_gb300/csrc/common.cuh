@@ -291,10 +291,12 @@ long long strip_rec_line_bytes(const GridDev &g);
 cudaError_t launch_fwd_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
                              const float *coef, void *scratch, float *sino, int *slow_rows, cudaStream_t s,
                              const StripRec *rec = nullptr);
-// Adjoint with strip accumulators; coef_out is overwritten.
+// Adjoint with strip accumulators; coef_out is overwritten.  `defer` holds
+// 2 + strip_chunk_count(L) words (chunks deferred to float strips).
+int64_t strip_chunk_count(const LinesDev &L);
 cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
                              const float *sino, void *scratch, float *coef_out, int *slow_rows, cudaStream_t s,
-                             const StripRec *rec = nullptr);
+                             const StripRec *rec, unsigned *defer);
 // Pixel-driven adjoint (gather.cu): thread per node over all views, no
 // atomics; parallel and fan beams of degree >= 1.  coef_out is overwritten.
 bool gather_supported(const GridDev &g, const LinesDev &L);

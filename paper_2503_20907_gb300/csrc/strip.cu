@@ -916,19 +916,41 @@ __device__ __noinline__ void strip_chunk_float_adj(unsigned char *smem, const Gr
                                          vec, err, chunk, rec, rec_cap);
 }
 
-// One CTA per chunk.  The adjoint runs as two launches over all chunks: FM
-// kFmFixed (the fixed-point chunks, nearly all) and then kFmFloat (the rest;
-// its CTAs return after one look at their chunk's sinogram values).
+// One CTA per chunk.  The adjoint runs the fixed-point chunks (FM kFmFixed:
+// nearly all) and appends the others to defer[2..] (count defer[0]) for
+// strip_float_kernel.
 template <int DEG, bool ADJ, int RM, int FM = kFmAll>
 __global__ void __launch_bounds__(kThreads, 2)
 strip_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
              const float *__restrict__ coef, const float *__restrict__ coefT, float *__restrict__ sino,
              float *__restrict__ out, float *__restrict__ outT, int chunks_per_view, int vec, int *err,
-             unsigned char *rec, long long rec_cap)
+             unsigned char *rec, long long rec_cap, unsigned *defer)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    strip_chunk<DEG, ADJ, RM, FM>(smem, g, L, hdr, tabs, coef, coefT, sino, out, outT, chunks_per_view, vec, err,
-                                  (int)blockIdx.x, rec, rec_cap);
+    const bool ran = strip_chunk<DEG, ADJ, RM, FM>(smem, g, L, hdr, tabs, coef, coefT, sino, out, outT,
+                                                   chunks_per_view, vec, err, (int)blockIdx.x, rec, rec_cap);
+    if (FM == kFmFixed && !ran && threadIdx.x == 0) defer[2 + atomicAdd(defer, 1u)] = blockIdx.x;
+}
+
+// The deferred adjoint chunks (float strip accumulators): a small persistent
+// grid over defer[2 .. 2 + defer[0]), defer[1] its counter.
+template <int DEG, int RM>
+__global__ void __launch_bounds__(kThreads, 2)
+strip_float_kernel(GridDev g, LinesDev L, const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
+                   float *__restrict__ sino, float *__restrict__ out, float *__restrict__ outT, int chunks_per_view,
+                   int vec, int *err, unsigned char *rec, long long rec_cap, unsigned *defer)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned cur;
+    const unsigned n = defer[0];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) cur = atomicAdd(defer + 1, 1u);
+        __syncthreads();
+        if (cur >= n) break;
+        strip_chunk<DEG, true, RM, kFmFloat>(smem, g, L, hdr, tabs, nullptr, nullptr, sino, out, outT,
+                                             chunks_per_view, vec, err, (int)defer[2 + cur], rec, rec_cap);
+    }
 }
 
 // Persistent kernel over the chunks of several instances of one degree: each
@@ -1056,13 +1078,14 @@ __global__ void add_transposed_kernel(const float *__restrict__ inT, float *__re
 template <int DEG, bool ADJ>
 cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
                            const float *coef, float *imgT, float *sino, float *out, int *err, cudaStream_t s,
-                           const StripRec *rec = nullptr, int rmode = kRecNone)
+                           const StripRec *rec = nullptr, int rmode = kRecNone, unsigned *defer = nullptr)
 {
     const dim3 tb(32, 8), tg((g.nx + 31) / 32, (g.ny + 31) / 32);
     cudaError_t e;
     unsigned char *rb = (rec && rmode != kRecNone) ? rec->base : nullptr;
     const long long rcap = rb ? rec->line_bytes : 0;
     if (!rb) rmode = kRecNone;
+    if (ADJ && !defer) return cudaErrorInvalidValue;
     if (rmode == kRecWrite) {
         // records only: no image in or out
     } else if (!ADJ) {
@@ -1070,15 +1093,16 @@ cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *h
     } else {
         e = cudaMemsetAsync(out, 0, sizeof(float) * (size_t)g.nx * g.ny, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(imgT, 0, sizeof(float) * (size_t)g.nx * g.ny, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(defer, 0, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
     }
-    // the adjoint: fixed-point chunks, then (a second launch) float chunks
+    // the adjoint: fixed-point chunks, then (a small second launch) the
+    // chunks they deferred to float strips
     constexpr int FM1 = ADJ ? kFmFixed : kFmAll;
     auto kern = rmode == kRecRead ? strip_kernel<DEG, ADJ, kRecRead, FM1>
                 : rmode == kRecWrite ? strip_kernel<DEG, ADJ, (ADJ ? kRecNone : kRecWrite), FM1>
                                      : strip_kernel<DEG, ADJ, kRecNone, FM1>;
-    auto kern2 = rmode == kRecRead ? strip_kernel<DEG, ADJ, kRecRead, kFmFloat>
-                                   : strip_kernel<DEG, ADJ, kRecNone, kFmFloat>;
+    auto kern2 = rmode == kRecRead ? strip_float_kernel<DEG, kRecRead> : strip_float_kernel<DEG, kRecNone>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e == cudaSuccess && ADJ)
         e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
@@ -1091,12 +1115,17 @@ cudaError_t launch_strip_t(const GridDev &g, const LinesDev &L, const LineHdr *h
     const int vec = (g.nx % 4 == 0) && (g.ny % 4 == 0) && ((reinterpret_cast<uintptr_t>(img) & 15) == 0) &&
                     ((reinterpret_cast<uintptr_t>(imgT) & 15) == 0);
     kern<<<grid, kThreads, kSmemBytes, s>>>(g, L, hdr, tabs, coef, imgT, const_cast<float *>(sino), out, imgT, cpv,
-                                            vec, err, rb, rcap);
+                                            vec, err, rb, rcap, defer);
     e = cudaGetLastError();
     if (e == cudaSuccess && ADJ) {
-        kern2<<<grid, kThreads, kSmemBytes, s>>>(g, L, hdr, tabs, coef, imgT, const_cast<float *>(sino), out, imgT,
-                                                 cpv, vec, err, rb, rcap);
-        e = cudaGetLastError();
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const unsigned g2 = grid < (unsigned)sms ? grid : (unsigned)sms;
+        if (e == cudaSuccess)
+            kern2<<<g2, kThreads, kSmemBytes, s>>>(g, L, hdr, tabs, const_cast<float *>(sino), out, imgT, cpv, vec,
+                                                   err, rb, rcap, defer);
+        if (e == cudaSuccess) e = cudaGetLastError();
     }
     if (e == cudaSuccess && ADJ && rmode != kRecWrite) {
         add_transposed_kernel<<<tg, tb, 0, s>>>(imgT, out, g.nx, g.ny);
@@ -1204,18 +1233,20 @@ cudaError_t launch_fwd_strip(const GridDev &g, const LinesDev &L, const LineHdr 
     }
 }
 
+int64_t strip_chunk_count(const LinesDev &L) { return chunk_views(L) * ((chunk_bins(L) + kChunk - 1) / kChunk); }
+
 cudaError_t launch_adj_strip(const GridDev &g, const LinesDev &L, const LineHdr *hdr, const float *tabs,
                              const float *sino, void *scratch, float *coef_out, int *err, cudaStream_t s,
-                             const StripRec *rec)
+                             const StripRec *rec, unsigned *defer)
 {
     float *outT = static_cast<float *>(scratch);
     float *p = const_cast<float *>(sino);
     const int rm = rec ? kRecRead : kRecNone;
     switch (g.kdeg) {
-    case 0: return launch_strip_t<0, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm);
-    case 1: return launch_strip_t<1, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm);
-    case 2: return launch_strip_t<2, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm);
-    default: return launch_strip_t<3, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm);
+    case 0: return launch_strip_t<0, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm, defer);
+    case 1: return launch_strip_t<1, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm, defer);
+    case 2: return launch_strip_t<2, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm, defer);
+    default: return launch_strip_t<3, true>(g, L, hdr, tabs, nullptr, outT, p, coef_out, err, s, rec, rm, defer);
     }
 }
 
