@@ -592,10 +592,11 @@ __device__ __forceinline__ bool strip_chunk(unsigned char *smem, const GridDev g
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) pm = fmaxf(pm, __shfl_xor_sync(0xffffffffu, pm, o));
             const float top = kPhiBound * g.h * pm;   // largest |h p phi| of the chunk
-            const bool fix = !__any_sync(0xffffffffu, bad) && top >= 1e-20f && top <= 1e20f;
+            // (an all-zero chunk counts as fixed point: its lines are skipped)
+            const bool fix = !__any_sync(0xffffffffu, bad) && (top == 0.f || (top >= 1e-20f && top <= 1e20f));
             if (lane == 0) {
                 int e = 0;
-                if (fix) {
+                if (fix && top > 0.f) {
                     frexpf(kFixMax / top, &e);   // kFixMax / top in [2^(e-1), 2^e)
                     e -= 1;                      // S = 2^e <= kFixMax / top
                 }
