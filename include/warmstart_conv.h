@@ -24,9 +24,9 @@ extern "C" {
 #endif
 
 /* Forward: y BF16 [B][H][W][cout] (FP32 [B][H][W] when cout = 1); relu != 0
- * clamps at 0 after the bias.  32 -> 32 runs on the tensor cores
- * (mma.sync, BF16 inputs, FP32 accumulation); 1 -> 32 and 32 -> 1 on the
- * CUDA cores. */
+ * clamps at 0 after the bias.  32 -> 32 runs on the fifth-generation tensor
+ * cores (tcgen05.mma, BF16 inputs, FP32 accumulators in tensor memory; 128
+ * pixels of a row per CTA); 1 -> 32 and 32 -> 1 on the CUDA cores. */
 sp_status sp_conv3x3_fwd(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,
                          int32_t dilation, const void *x, const void *w, const float *bias, int32_t relu,
                          void *y, void *stream);

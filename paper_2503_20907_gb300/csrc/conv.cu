@@ -4,11 +4,15 @@
 //
 // Taps may be dilated (offsets -d, 0, d).
 //
-//   forward, 32 -> 32 channels: implicit GEMM on the tensor cores
-//     (mma.sync m16n8k16, BF16 in, FP32 accumulate).  A CTA takes 64 pixels
-//     of one image row; the three input rows it needs and the weights are
-//     staged in shared memory with padded strides (no bank conflicts on the
-//     fragment loads).  Epilogue: bias, optional ReLU, BF16 store.
+//   forward, 32 -> 32 channels: implicit GEMM on the fifth-generation
+//     tensor cores (conv32_tc05_kernel: tcgen05.mma, BF16 in, FP32
+//     accumulators in tensor memory, read back with tcgen05.ld).  A CTA
+//     takes 128 pixels of one image row; the three input rows it needs and
+//     the weights are staged in shared memory in the canonical K-major
+//     layout, so each tap's operand is the staged rows read from another
+//     start address.  Epilogue: bias, optional ReLU, BF16 store.
+//   conv32_fwd_kernel (mma.sync m16n8k16, 64 pixels per CTA, padded
+//     strides against bank conflicts) serves the input gradient below.
 //   forward, 1 -> 32 and 32 -> 1: CUDA cores, thread per pixel.
 //   gradients of the 32 -> 32 layers (training), on the tensor cores too:
 //     the input gradient is the same kernel run on the incoming gradient g
@@ -411,6 +415,178 @@ __global__ void flip_weights_kernel(const bf16 *__restrict__ w, bf16 *__restrict
     }
 }
 
+// ------------------------------------------------------------------ tcgen05
+// The 32 -> 32 forward on the fifth-generation tensor cores: one CTA of 4
+// warps computes 128 output pixels of one image row as D[128 x 32] =
+// sum over the 18 K-steps (9 taps x 2 halves of 16 input channels) of
+// A_s[128 x 16] B_s[16 x 32]^T, one tcgen05.mma (kind::f16, BF16 in, FP32
+// accumulators in tensor memory) per step, issued by one thread.
+//
+// Shared-memory operands use the canonical no-swizzle K-major layout: core
+// matrices of 8 rows x 16 bytes stored contiguously (128 bytes), LBO the
+// byte distance between core matrices along K, SBO along M (or N).
+//   input  xs[cg][row][pixel][8]: channel group cg (8 channels) of the three
+//          rows h - d, h, h + d and pixels w0 - d .. w0 + 127 + d.  A tap's
+//          A operand is the same array read from another start address:
+//          LBO = one channel group (kXRows5 * kXPix5 * 16 B), SBO = 128 B
+//          (8 pixels of 16 B).
+//   weights wb[kc][n][8]: K = tap 32 + input channel in groups kc of 8,
+//          n the output channel; LBO = 32 * 16 B, SBO = 128 B.
+constexpr int kTile5 = 128;                  // output pixels of one CTA (M)
+constexpr int kXPix5 = kTile5 + 2 * kMaxDil;  // staged pixels per row
+constexpr int kXRows5 = 3;
+constexpr int kXBytes5 = 4 * kXRows5 * kXPix5 * 16;   // 30,720
+constexpr int kWBytes5 = 36 * kC * 16;                // 18,432
+constexpr int kSmem5 = kXBytes5 + kWBytes5 + 16;      // + mbarrier and TMEM address
+constexpr uint32_t kTmemCols5 = 32;                   // FP32 accumulators: N = 32 columns
+
+__device__ __forceinline__ uint32_t s_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, LBO and SBO in 16-byte
+// units, the descriptor version of this architecture (bits 46-47 = 1), no
+// swizzle (layout type 0), base offset 0.
+__host__ __device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
+// 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(uint32_t M, uint32_t N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// y = conv(x) + bias (ReLU optional), 32 -> 32 channels, taps dil apart, on
+// tcgen05.  128 threads; warp w reads the accumulators of pixels 32w..32w+31
+// (tensor-memory lanes 32w..).  Every wait is bounded; a CTA whose MMAs did
+// not complete writes NaN and still frees its tensor memory.
+__global__ void __launch_bounds__(128) conv32_tc05_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
+                                                          const float *__restrict__ bias, bf16 *__restrict__ y,
+                                                          int B, int H, int W, int relu, int dil)
+{
+    extern __shared__ __align__(128) unsigned char sm5[];
+    unsigned char *xs = sm5;
+    unsigned char *wsb = sm5 + kXBytes5;
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(sm5 + kXBytes5 + kWBytes5);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_w = (W + kTile5 - 1) / kTile5;
+    const int tw = blockIdx.x % tiles_w;
+    const int h = (blockIdx.x / tiles_w) % H;
+    const int b = blockIdx.x / (tiles_w * H);
+    const int w0 = tw * kTile5;
+
+    // tensor memory (warp 0) and the MMA completion barrier (thread 0)
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(tslot)),
+                     "r"(kTmemCols5)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // weights: wb[kc][n][8] = W[n][kc 8 .. kc 8 + 7] (W is [n][tap][i], K = tap 32 + i)
+    for (int i = threadIdx.x; i < 36 * kC; i += 128) {
+        const int kc = i / kC, n = i - kc * kC;
+        *reinterpret_cast<uint4 *>(wsb + (kc * kC + n) * 16) =
+            *reinterpret_cast<const uint4 *>(w + (size_t)n * 9 * kC + kc * 8);
+    }
+    // input rows h - d, h, h + d; pixels w0 - d .. w0 + 127 + d; zero outside
+    const int tw2 = kTile5 + 2 * dil;
+    for (int i = threadIdx.x; i < kXRows5 * tw2 * 4; i += 128) {
+        const int r = i / (tw2 * 4), rem = i - r * tw2 * 4;
+        const int p = rem >> 2, cg = rem & 3;
+        const int hh = h + (r - 1) * dil, ww = w0 + p - dil;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (hh >= 0 && hh < H && ww >= 0 && ww < W)
+            v = *reinterpret_cast<const uint4 *>(x + (((size_t)b * H + hh) * W + ww) * kC + cg * 8);
+        *reinterpret_cast<uint4 *>(xs + ((cg * kXRows5 + r) * kXPix5 + p) * 16) = v;
+    }
+    // generic-proxy shared stores visible to the tensor cores, then sync
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = *tslot;
+
+    if (threadIdx.x == 0) {
+        constexpr uint32_t idesc = umma_idesc_bf16(kTile5, kC);
+        const uint32_t xbase = s_u32(xs), wbase = s_u32(wsb);
+        constexpr uint32_t kGroup = kXRows5 * kXPix5 * 16;   // A: LBO (next 8 channels)
+#pragma unroll 1
+        for (int s = 0; s < 18; ++s) {
+            const int tap = s >> 1, half = s & 1;
+            const int ky = tap / 3, kx = tap - 3 * ky;
+            const uint32_t a_addr = xbase + (uint32_t)(2 * half) * kGroup + (uint32_t)(ky * kXPix5 * 16) +
+                                    (uint32_t)(kx * dil) * 16u;
+            const uint64_t adesc = umma_smem_desc(a_addr, kGroup, 128);
+            const uint64_t bdesc = umma_smem_desc(wbase + (uint32_t)s * 2u * kC * 16u, kC * 16, 128);
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+                         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(s)
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         s_u32(mbar))
+                     : "memory");
+    }
+    // wait (bounded) for the MMAs
+    bool done = false;
+    for (int it = 0; it < (1 << 24) && !done; ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(s_u32(mbar))
+                     : "memory");
+        done = ok != 0;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // accumulators of this warp's 32 pixels: 32 columns (output channels)
+    uint32_t acc[kC];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                 "[%32];"
+                 : "=r"(acc[0]), "=r"(acc[1]), "=r"(acc[2]), "=r"(acc[3]), "=r"(acc[4]), "=r"(acc[5]),
+                   "=r"(acc[6]), "=r"(acc[7]), "=r"(acc[8]), "=r"(acc[9]), "=r"(acc[10]), "=r"(acc[11]),
+                   "=r"(acc[12]), "=r"(acc[13]), "=r"(acc[14]), "=r"(acc[15]), "=r"(acc[16]), "=r"(acc[17]),
+                   "=r"(acc[18]), "=r"(acc[19]), "=r"(acc[20]), "=r"(acc[21]), "=r"(acc[22]), "=r"(acc[23]),
+                   "=r"(acc[24]), "=r"(acc[25]), "=r"(acc[26]), "=r"(acc[27]), "=r"(acc[28]), "=r"(acc[29]),
+                   "=r"(acc[30]), "=r"(acc[31])
+                 : "r"(taddr + ((uint32_t)(warp * 32) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    // epilogue: pixel w0 + 32 warp + lane, 32 channels = 64 bytes
+    const int ww = w0 + warp * 32 + lane;
+    if (ww < W) {
+        uint4 out[4];
+        __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(out);
+#pragma unroll
+        for (int o = 0; o < kC; o += 2) {
+            float v0 = done ? __uint_as_float(acc[o]) : __int_as_float(0x7fc00000);
+            float v1 = done ? __uint_as_float(acc[o + 1]) : __int_as_float(0x7fc00000);
+            if (bias) { v0 += bias[o]; v1 += bias[o + 1]; }
+            if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+            o2[o >> 1] = __floats2bfloat162_rn(v0, v1);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(y + (((size_t)b * H + h) * W + ww) * kC);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = out[k];
+    }
+    // free the tensor memory once every warp's loads are done
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols5)
+                     : "memory");
+    }
+}
+
 }  // namespace
 }  // namespace spx
 
@@ -430,11 +606,15 @@ sp_status sp_conv3x3_fwd(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t c
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const spx::bf16 *xb = static_cast<const spx::bf16 *>(x), *wb = static_cast<const spx::bf16 *>(w);
     if (inner) {
-        const int tiles = (W + spx::kTileW - 1) / spx::kTileW;
+        // tcgen05 (tensor memory accumulators), 128 pixels of a row per CTA
+        const int tiles = (W + spx::kTile5 - 1) / spx::kTile5;
         const int64_t grid = (int64_t)B * H * tiles;
         if (grid > 0x7fffffff) return spx::record_error(SP_EINVAL, "too many tiles");
-        spx::conv32_fwd_kernel<false><<<(unsigned)grid, 128, 0, s>>>(xb, wb, bias, y, B, H, W, relu, dilation,
-                                                                    nullptr);
+        cudaError_t ea = cudaFuncSetAttribute(spx::conv32_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              spx::kSmem5);
+        if (ea != cudaSuccess) return spx::record_error(SP_ECUDA, cudaGetErrorString(ea));
+        spx::conv32_tc05_kernel<<<(unsigned)grid, 128, spx::kSmem5, s>>>(xb, wb, bias, static_cast<spx::bf16 *>(y),
+                                                                         B, H, W, relu, dilation);
     } else {
         const int64_t n = (int64_t)B * H * W;
         int64_t blocks = (n + 255) / 256;

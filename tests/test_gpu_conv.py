@@ -1,8 +1,9 @@
 """The warm-start network's convolution kernels (include/warmstart_conv.h)
-against the FP64 oracle layers on BF16-exact inputs: the forward (tensor
-cores for 32 -> 32, CUDA cores for the edge layers, ragged tiles), both
-gradients, the autograd wrapper, and exact integer sums that pin the
-tensor-core fragment layout."""
+against the FP64 oracle layers on BF16-exact inputs: the forward (tcgen05
+tensor cores for 32 -> 32, CUDA cores for the edge layers, ragged tiles of
+128 pixels), both gradients, the autograd wrapper, and exact integer sums
+that pin the tensor-core operand layouts (shared-memory descriptors, tensor
+memory lanes)."""
 import numpy as np
 import pytest
 
@@ -34,7 +35,8 @@ def _fwd(x, w, b, relu, cout, d=1):
     return y
 
 
-@pytest.mark.parametrize("H,W,d", [(5, 70, 1), (3, 64, 1), (4, 17, 1), (9, 70, 4), (20, 40, 16)])
+@pytest.mark.parametrize("H,W,d", [(5, 70, 1), (3, 64, 1), (4, 17, 1), (9, 70, 4), (20, 40, 16), (3, 256, 1),
+                                   (4, 130, 5), (35, 129, 16)])
 def test_conv32_exact_integer_sums(H, W, d):
     # small integers: every product and partial sum is exact in FP32 and the
     # result (|y| < 256) exact in BF16, so the tensor-core result must equal
