@@ -34,9 +34,9 @@ sp_status sp_conv3x3_fwd(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t c
 /* Input gradient: dx[b,h,w,i] = sum_{ky,kx,o} g[b,h-(ky-1)d,w-(kx-1)d,o] W[o,ky,kx,i]
  * with g FP32 [B][H][W][cout] and dx FP32 [B][H][W][cin]; if gate != NULL
  * (BF16 [B][H][W][cin]) dx is zeroed where gate <= 0 (ReLU of the layer
- * below).  32 -> 32 runs on the tensor cores (g rounded to BF16, FP32
- * accumulation; g, w, dx 16-byte aligned); the others on the CUDA cores in
- * FP32. */
+ * below).  32 -> 32 runs on the tcgen05 tensor cores (g rounded to BF16,
+ * FP32 accumulation in tensor memory; g, w, dx and gate 16-byte aligned);
+ * the others on the CUDA cores in FP32. */
 sp_status sp_conv3x3_bwd_data(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,
                               int32_t dilation, const float *g, const void *w, const void *gate, float *dx,
                               void *stream);

@@ -11,17 +11,15 @@
 //     the weights are staged in shared memory in the canonical K-major
 //     layout, so each tap's operand is the staged rows read from another
 //     start address.  Epilogue: bias, optional ReLU, BF16 store.
-//   conv32_fwd_kernel (mma.sync m16n8k16, 64 pixels per CTA, padded
-//     strides against bank conflicts) serves the input gradient below.
 //   forward, 1 -> 32 and 32 -> 1: CUDA cores, thread per pixel.
 //   gradients of the 32 -> 32 layers (training), on the tensor cores too:
-//     the input gradient is the same kernel run on the incoming gradient g
-//     (rounded to BF16 while it is staged) with the weights flipped while
-//     they are staged (W'[i, 8 - tap, o] = W[o, tap, i]), FP32 output gated
-//     by the ReLU of the layer below; the weight gradient is a GEMM over the
-//     pixels (M = 32 output channels, N = 9 taps x 32 input channels, K =
-//     pixels) with g and x staged transposed, one partial sum per block
-//     added to the result.
+//     the input gradient is the same tcgen05 kernel run on the incoming
+//     gradient g (rounded to BF16 while it is staged) with the weights
+//     flipped while they are staged (W'[i, 8 - tap, o] = W[o, tap, i]), FP32
+//     output gated by the ReLU of the layer below; the weight gradient is a
+//     GEMM over the pixels (M = 32 output channels, N = 9 taps x 32 input
+//     channels, K = pixels) with g and x staged transposed, on mma.sync
+//     (m16n8k16), one partial sum per block added to the result.
 //   gradients of the 1 -> 32 and 32 -> 1 layers: CUDA cores in FP32.
 #include <cuda_bf16.h>
 
@@ -37,9 +35,6 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int kC = 32;              // channels of the inner layers
-constexpr int kTileW = 64;          // pixels of one CTA (4 warps x 16)
-constexpr int kXStride = 40;        // bf16 per staged pixel (32 + 8: conflict-free fragment loads)
-constexpr int kWStride = 9 * kC + 8;   // bf16 per staged output channel
 constexpr int kMaxDil = 16;         // largest dilation of the taps
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
@@ -50,115 +45,6 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
         "{%0, %1, %2, %3};"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// y = conv(x) + bias (ReLU optional), 32 -> 32 channels, taps dil apart.
-// GRAD: the input gradient instead: x is the FP32 gradient g of the layer's
-// output (rounded to BF16 here), w the layer's weights (flipped here), y the
-// FP32 gradient of its input, zeroed where gate <= 0 (gate may be NULL).
-template <bool GRAD>
-__global__ void __launch_bounds__(128) conv32_fwd_kernel(const void *__restrict__ xv, const bf16 *__restrict__ w,
-                                                         const float *__restrict__ bias, void *__restrict__ yv,
-                                                         int B, int H, int W, int relu, int dil,
-                                                         const bf16 *__restrict__ gate)
-{
-    __shared__ __align__(16) bf16 xs[3][kTileW + 2 * kMaxDil][kXStride];
-    __shared__ __align__(16) bf16 ws[kC][kWStride];
-    const int tiles_w = (W + kTileW - 1) / kTileW;
-    const int tw = blockIdx.x % tiles_w;
-    const int h = (blockIdx.x / tiles_w) % H;
-    const int b = blockIdx.x / (tiles_w * H);
-    const int w0 = tw * kTileW;
-    if constexpr (!GRAD) {
-        // weights: 32 x 288 bf16, 16-byte chunks (36 per channel)
-        for (int i = threadIdx.x; i < kC * 36; i += 128) {
-            const int o = i / 36, c = i - o * 36;
-            *reinterpret_cast<uint4 *>(&ws[o][c * 8]) =
-                *reinterpret_cast<const uint4 *>(w + (size_t)o * 9 * kC + c * 8);
-        }
-    } else {
-        // flipped: ws[i][(8 - tap) 32 + o] = W[o][tap][i], read in 16-byte chunks of 8 i
-        for (int j = threadIdx.x; j < kC * 36; j += 128) {
-            const int o = j / 36, rem = j - o * 36, tap = rem >> 2, i0 = (rem & 3) * 8;
-            const uint4 v = *reinterpret_cast<const uint4 *>(w + ((size_t)o * 9 + tap) * kC + i0);
-            const bf16 *e = reinterpret_cast<const bf16 *>(&v);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) ws[i0 + k][(8 - tap) * kC + o] = e[k];
-        }
-    }
-    // input rows h-dil, h, h+dil, pixels w0-dil..w0+63+dil, 16-byte chunks of 8 channels
-    const int tw2 = kTileW + 2 * dil;
-    for (int i = threadIdx.x; i < 3 * tw2 * 4; i += 128) {
-        const int r = i / (tw2 * 4), rem = i - r * tw2 * 4;
-        const int p = rem >> 2, c = rem & 3;
-        const int hh = h + (r - 1) * dil, ww = w0 + p - dil;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (hh >= 0 && hh < H && ww >= 0 && ww < W) {
-            const size_t off = (((size_t)b * H + hh) * W + ww) * kC + c * 8;
-            if constexpr (GRAD) {
-                const float4 f0 = *reinterpret_cast<const float4 *>(static_cast<const float *>(xv) + off);
-                const float4 f1 = *reinterpret_cast<const float4 *>(static_cast<const float *>(xv) + off + 4);
-                __nv_bfloat162 q[4] = {__floats2bfloat162_rn(f0.x, f0.y), __floats2bfloat162_rn(f0.z, f0.w),
-                                       __floats2bfloat162_rn(f1.x, f1.y), __floats2bfloat162_rn(f1.z, f1.w)};
-                v = *reinterpret_cast<const uint4 *>(q);
-            } else {
-                v = *reinterpret_cast<const uint4 *>(static_cast<const bf16 *>(xv) + off);
-            }
-        }
-        *reinterpret_cast<uint4 *>(&xs[r][p][c * 8]) = v;
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int pb = warp * 16;   // first pixel of the warp in the tile
-    float acc[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[nt][k] = 0.f;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap - 3 * (tap / 3);
-#pragma unroll
-        for (int cb = 0; cb < 2; ++cb) {
-            const int c0 = cb * 16 + 2 * t;
-            const int px = pb + g + kx * dil;
-            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(&xs[ky][px][c0]);
-            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(&xs[ky][px + 8][c0]);
-            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(&xs[ky][px][c0 + 8]);
-            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(&xs[ky][px + 8][c0 + 8]);
-            const int k0 = tap * kC + cb * 16 + 2 * t;
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&ws[nt * 8 + g][k0]);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&ws[nt * 8 + g][k0 + 8]);
-                mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
-            }
-        }
-    }
-    // epilogue: (pixel pb+g, channels 2t, 2t+1) and (pixel pb+g+8, same)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const int o = nt * 8 + 2 * t;
-        const float b0 = bias ? bias[o] : 0.f, b1 = bias ? bias[o + 1] : 0.f;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int ww = w0 + pb + g + 8 * half;
-            if (ww >= W) continue;
-            float v0 = acc[nt][2 * half] + b0, v1 = acc[nt][2 * half + 1] + b1;
-            const size_t off = (((size_t)b * H + h) * W + ww) * kC + o;
-            if constexpr (GRAD) {
-                if (gate) {
-                    if (!(__bfloat162float(gate[off]) > 0.f)) v0 = 0.f;
-                    if (!(__bfloat162float(gate[off + 1]) > 0.f)) v1 = 0.f;
-                }
-                *reinterpret_cast<float2 *>(static_cast<float *>(yv) + off) = make_float2(v0, v1);
-            } else {
-                if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
-                *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(yv) + off) = __floats2bfloat162_rn(v0, v1);
-            }
-        }
-    }
 }
 
 __device__ __forceinline__ float ld_act(const bf16 *p) { return __bfloat162float(*p); }
@@ -463,9 +349,15 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(uint32_t M, uint32_t N)
 // tcgen05.  128 threads; warp w reads the accumulators of pixels 32w..32w+31
 // (tensor-memory lanes 32w..).  Every wait is bounded; a CTA whose MMAs did
 // not complete writes NaN and still frees its tensor memory.
-__global__ void __launch_bounds__(128) conv32_tc05_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
-                                                          const float *__restrict__ bias, bf16 *__restrict__ y,
-                                                          int B, int H, int W, int relu, int dil)
+// GRAD: the input gradient instead: x is the FP32 gradient g of the layer's
+// output (rounded to BF16 while staged), the weights are flipped while staged
+// (W'[i][8 - tap][o] = W[o][tap][i]), y is the FP32 gradient of the layer's
+// input, zeroed where gate <= 0 (gate may be NULL).
+template <bool GRAD>
+__global__ void __launch_bounds__(128) conv32_tc05_kernel(const void *__restrict__ xv, const bf16 *__restrict__ w,
+                                                          const float *__restrict__ bias, void *__restrict__ yv,
+                                                          int B, int H, int W, int relu, int dil,
+                                                          const bf16 *__restrict__ gate)
 {
     extern __shared__ __align__(128) unsigned char sm5[];
     unsigned char *xs = sm5;
@@ -490,11 +382,20 @@ __global__ void __launch_bounds__(128) conv32_tc05_kernel(const bf16 *__restrict
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // weights: wb[kc][n][8] = W[n][kc 8 .. kc 8 + 7] (W is [n][tap][i], K = tap 32 + i)
+    // weights: wb[kc][n][8] = W[n][kc 8 .. kc 8 + 7] (W is [n][tap][i], K = tap 32 + i);
+    // flipped for the input gradient: n = i, K = tap' 32 + o, W[o][8 - tap'][i]
     for (int i = threadIdx.x; i < 36 * kC; i += 128) {
         const int kc = i / kC, n = i - kc * kC;
-        *reinterpret_cast<uint4 *>(wsb + (kc * kC + n) * 16) =
-            *reinterpret_cast<const uint4 *>(w + (size_t)n * 9 * kC + kc * 8);
+        if constexpr (GRAD) {
+            const int tp = kc >> 2, o0 = (kc & 3) * 8;
+            __align__(16) bf16 e[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) e[j] = w[((size_t)(o0 + j) * 9 + (8 - tp)) * kC + n];
+            *reinterpret_cast<uint4 *>(wsb + (kc * kC + n) * 16) = *reinterpret_cast<const uint4 *>(e);
+        } else {
+            *reinterpret_cast<uint4 *>(wsb + (kc * kC + n) * 16) =
+                *reinterpret_cast<const uint4 *>(w + (size_t)n * 9 * kC + kc * 8);
+        }
     }
     // input rows h - d, h, h + d; pixels w0 - d .. w0 + 127 + d; zero outside
     const int tw2 = kTile5 + 2 * dil;
@@ -503,8 +404,18 @@ __global__ void __launch_bounds__(128) conv32_tc05_kernel(const bf16 *__restrict
         const int p = rem >> 2, cg = rem & 3;
         const int hh = h + (r - 1) * dil, ww = w0 + p - dil;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (hh >= 0 && hh < H && ww >= 0 && ww < W)
-            v = *reinterpret_cast<const uint4 *>(x + (((size_t)b * H + hh) * W + ww) * kC + cg * 8);
+        if (hh >= 0 && hh < H && ww >= 0 && ww < W) {
+            const size_t off = (((size_t)b * H + hh) * W + ww) * kC + cg * 8;
+            if constexpr (GRAD) {
+                const float4 f0 = *reinterpret_cast<const float4 *>(static_cast<const float *>(xv) + off);
+                const float4 f1 = *reinterpret_cast<const float4 *>(static_cast<const float *>(xv) + off + 4);
+                __nv_bfloat162 q[4] = {__floats2bfloat162_rn(f0.x, f0.y), __floats2bfloat162_rn(f0.z, f0.w),
+                                       __floats2bfloat162_rn(f1.x, f1.y), __floats2bfloat162_rn(f1.z, f1.w)};
+                v = *reinterpret_cast<const uint4 *>(q);
+            } else {
+                v = *reinterpret_cast<const uint4 *>(static_cast<const bf16 *>(xv) + off);
+            }
+        }
         *reinterpret_cast<uint4 *>(xs + ((cg * kXRows5 + r) * kXPix5 + p) * 16) = v;
     }
     // generic-proxy shared stores visible to the tensor cores, then sync
@@ -562,7 +473,28 @@ __global__ void __launch_bounds__(128) conv32_tc05_kernel(const bf16 *__restrict
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     // epilogue: pixel w0 + 32 warp + lane, 32 channels = 64 bytes
     const int ww = w0 + warp * 32 + lane;
-    if (ww < W) {
+    if (GRAD && ww < W) {
+        const size_t off = (((size_t)b * H + h) * W + ww) * kC;
+        float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(yv) + off);
+        uint4 gt[4];
+        if (gate) {
+            const uint4 *gp = reinterpret_cast<const uint4 *>(gate + off);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gt[k] = gp[k];
+        }
+        const bf16 *ge = reinterpret_cast<const bf16 *>(gt);
+#pragma unroll
+        for (int o = 0; o < kC; o += 4) {
+            float v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                v[j] = done ? __uint_as_float(acc[o + j]) : __int_as_float(0x7fc00000);
+                if (gate && !(__bfloat162float(ge[o + j]) > 0.f)) v[j] = 0.f;
+            }
+            dst[o >> 2] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    }
+    if (!GRAD && ww < W) {
         uint4 out[4];
         __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(out);
 #pragma unroll
@@ -573,7 +505,7 @@ __global__ void __launch_bounds__(128) conv32_tc05_kernel(const bf16 *__restrict
             if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
             o2[o >> 1] = __floats2bfloat162_rn(v0, v1);
         }
-        uint4 *dst = reinterpret_cast<uint4 *>(y + (((size_t)b * H + h) * W + ww) * kC);
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<bf16 *>(yv) + (((size_t)b * H + h) * W + ww) * kC);
 #pragma unroll
         for (int k = 0; k < 4; ++k) dst[k] = out[k];
     }
@@ -610,11 +542,11 @@ sp_status sp_conv3x3_fwd(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t c
         const int tiles = (W + spx::kTile5 - 1) / spx::kTile5;
         const int64_t grid = (int64_t)B * H * tiles;
         if (grid > 0x7fffffff) return spx::record_error(SP_EINVAL, "too many tiles");
-        cudaError_t ea = cudaFuncSetAttribute(spx::conv32_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              spx::kSmem5);
+        cudaError_t ea = cudaFuncSetAttribute(spx::conv32_tc05_kernel<false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, spx::kSmem5);
         if (ea != cudaSuccess) return spx::record_error(SP_ECUDA, cudaGetErrorString(ea));
-        spx::conv32_tc05_kernel<<<(unsigned)grid, 128, spx::kSmem5, s>>>(xb, wb, bias, static_cast<spx::bf16 *>(y),
-                                                                         B, H, W, relu, dilation);
+        spx::conv32_tc05_kernel<false><<<(unsigned)grid, 128, spx::kSmem5, s>>>(xb, wb, bias, y, B, H, W, relu,
+                                                                                dilation, nullptr);
     } else {
         const int64_t n = (int64_t)B * H * W;
         int64_t blocks = (n + 255) / 256;
@@ -643,10 +575,16 @@ sp_status sp_conv3x3_bwd_data(int32_t B, int32_t H, int32_t W, int32_t cin, int3
     if (cin == 32 && cout == 32) {
         if ((reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(dx)) & 15)
             return spx::record_error(SP_EINVAL, "g, w, dx must be 16-byte aligned");
-        const int tiles = (W + spx::kTileW - 1) / spx::kTileW;
+        const int tiles = (W + spx::kTile5 - 1) / spx::kTile5;
         const int64_t grid = (int64_t)B * H * tiles;
         if (grid > 0x7fffffff) return spx::record_error(SP_EINVAL, "too many tiles");
-        spx::conv32_fwd_kernel<true><<<(unsigned)grid, 128, 0, s>>>(g, wb, nullptr, dx, B, H, W, 0, dilation, gb);
+        if (gate && (reinterpret_cast<uintptr_t>(gate) & 15))
+            return spx::record_error(SP_EINVAL, "gate must be 16-byte aligned");
+        cudaError_t ea = cudaFuncSetAttribute(spx::conv32_tc05_kernel<true>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, spx::kSmem5);
+        if (ea != cudaSuccess) return spx::record_error(SP_ECUDA, cudaGetErrorString(ea));
+        spx::conv32_tc05_kernel<true><<<(unsigned)grid, 128, spx::kSmem5, s>>>(g, wb, nullptr, dx, B, H, W, 0,
+                                                                               dilation, gb);
     } else if (cin == 32)
         spx::conv_dgrad_kernel<32, 1><<<(unsigned)blocks, 128, 0, s>>>(g, wb, gb, dx, B, H, W, dilation);
     else
