@@ -696,7 +696,7 @@ struct sp_batch {
     // jobs [gjob0, gjob0 + gnjob) of group deg own gtotal chunks
     int gjob0[2][4] = {}, gnjob[2][4] = {};
     int64_t gtotal[2][4] = {};
-    unsigned long long *counter = nullptr;              // [2][3 degrees][3]: queue counters
+    unsigned long long *counter = nullptr;              // [2][4 degrees][3]: queue counters
     long long *defer = nullptr;                          // adjoint chunks deferred to float strips
     int64_t defer_cap = 0;
 };
@@ -779,14 +779,13 @@ cudaError_t upload_jobs(sp_batch *b, int d, In in, Out outp, std::vector<char> &
     hj.clear();
     queued.assign(b->plans.size(), 0);
     int64_t all = 0;
-    for (int deg = 1; deg <= 3; ++deg) {
+    for (int deg = 0; deg <= 3; ++deg) {
         b->gjob0[d][deg] = (int)hj.size();
         int64_t c0 = 0;   // chunk indices count within the degree's group
         for (size_t i = 0; i < b->plans.size(); ++i) {
             const sp_plan *p = b->plans[i];
             const int path = d ? p->path_adj : p->path_fwd;
-            // degree 0 (strip kernels only when set or tuned) keeps its own
-            // launch: the queue kernels carry degrees 1-3
+            // (degree 0 takes the strip kernels when set or tuned to them)
             if (p->g.kdeg != deg || p->L.m == 0 || !use_strip(p->g, p->L, p->extra, path)) continue;
             spx::StripJob J = d ? spx::make_strip_job(p->g, p->L, p->hdr, p->tabs, true, nullptr,
                                                       const_cast<float *>(in[i]), outp[i], p->extra,
@@ -825,10 +824,10 @@ cudaError_t run_queue(sp_batch *b, int d, cudaStream_t s)
     cudaError_t e = cudaSuccess;
     for (size_t k = 0; k < hj.size() && e == cudaSuccess; ++k) e = spx::launch_strip_pre(hj[k], d == 1, s);
     int64_t defer0 = 0;   // each degree's deferred chunks in its own part of the list
-    for (int deg = 1; deg <= 3 && e == cudaSuccess; ++deg) {
+    for (int deg = 0; deg <= 3 && e == cudaSuccess; ++deg) {
         if (b->gnjob[d][deg] == 0) continue;
         e = spx::launch_strip_queue(deg, d == 1, b->jobs_dev[d] + b->gjob0[d][deg], b->gnjob[d][deg],
-                                    b->gtotal[d][deg], b->counter + 9 * d + 3 * (deg - 1),
+                                    b->gtotal[d][deg], b->counter + 12 * d + 3 * deg,
                                     d == 1 ? b->defer + defer0 : nullptr, s);
         defer0 += b->gtotal[d][deg];
     }
@@ -860,7 +859,7 @@ sp_status spline_batch_create(int32_t count, const sp_grid *grids, const sp_line
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     for (int d = 0; d < 2 && e == cudaSuccess; ++d) e = cudaMalloc(&b->jobs_dev[d], sizeof(spx::StripJob) * (size_t)count);
-    if (e == cudaSuccess) e = cudaMalloc(&b->counter, 18 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->counter, 24 * sizeof(unsigned long long));
     for (int k = 0; k < kBatchStreams && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);

@@ -332,7 +332,7 @@ int64_t strip_job_chunks(const StripJob &J);
 cudaError_t launch_strip_pre(const StripJob &J, bool adj, cudaStream_t s);
 cudaError_t launch_strip_post(const StripJob &J, bool adj, cudaStream_t s);
 // The persistent kernel over jobs[0..njobs) (device array, chunk0 ascending,
-// `total` chunks in all, every job of kernel degree deg in 1..3); counter is
+// `total` chunks in all, every job of kernel degree deg in 0..3); counter is
 // three device words, reset here.  The adjoint defers chunks that need float
 // strips to `defer` (device, room for `total` chunk indices) and runs them in
 // a second launch.

@@ -1185,7 +1185,7 @@ cudaError_t launch_strip_queue(int deg, bool adj, const StripJob *jobs, int njob
                                unsigned long long *counter, long long *defer, cudaStream_t s)
 {
     if (njobs <= 0 || total <= 0) return cudaSuccess;
-    if (deg < 1 || deg > 3 || (adj && !defer)) return cudaErrorInvalidValue;
+    if (deg < 0 || deg > 3 || (adj && !defer)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1194,6 +1194,7 @@ cudaError_t launch_strip_queue(int deg, bool adj, const StripJob *jobs, int njob
     int64_t grid = 2 * (int64_t)sms;   // two CTAs per SM, resident at once
     if (grid > total) grid = total;
     switch (deg) {
+    case 0: return launch_queue_t<0>(adj, jobs, njobs, total, counter, defer, grid, sms, s);
     case 1: return launch_queue_t<1>(adj, jobs, njobs, total, counter, defer, grid, sms, s);
     case 2: return launch_queue_t<2>(adj, jobs, njobs, total, counter, defer, grid, sms, s);
     default: return launch_queue_t<3>(adj, jobs, njobs, total, counter, defer, grid, sms, s);

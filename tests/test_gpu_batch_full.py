@@ -38,10 +38,10 @@ def full_batch():
 
 def test_full_batch_ran_through_queue(full_batch):
     ws, grids, lines, batch, paths, sinos, backs = full_batch
-    # the queue carries degrees 1-3 of every line-list kind (degree 0 on the
-    # strip kernels keeps its own launch)
-    n_fwd = sum(1 for (f, _), g in zip(paths, grids) if f == 1 and g.degree >= 1)
-    n_adj = sum(1 for (_, a), g in zip(paths, grids) if a == 1 and g.degree >= 1)
+    # the queue kernels carry every instance on the strip kernels (one
+    # persistent launch per degree and direction), any line-list kind
+    n_fwd = sum(1 for (f, _) in paths if f == 1)
+    n_adj = sum(1 for (_, a) in paths if a == 1)
     assert batch.queued(False) == n_fwd and batch.queued(True) == n_adj
     assert n_adj > 0
 
