@@ -528,20 +528,13 @@ __device__ float strip_line(const LineHdr &H, const float *tabw, float *ent_t, i
 // transposed image).
 // One chunk (view v, bins j0..j0+31) of one instance; smem is the CTA's
 // dynamic shared memory (kSmemBytes).
-template <int DEG, int RM>
-__device__ __noinline__ void strip_chunk_float_adj(unsigned char *smem, const GridDev g, const LinesDev L,
-                                                   const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
-                                                   float *__restrict__ sino, float *__restrict__ out,
-                                                   float *__restrict__ outT, int chunks_per_view, int vec, int *err,
-                                                   int chunk, unsigned char *rec, long long rec_cap);
-
-// FM (adjoint only) picks the chunks a call runs and their accumulators:
-// kFmAll runs every chunk, those that need float accumulators (see the top
-// of the file) through an out-of-line copy with float strips; kFmFixed runs
-// only the fixed-point chunks and kFmFloat only the others, so that a
-// launch of each covers every chunk and the fixed-point kernel carries no
-// second copy of the line code (a second inlined copy, or a call anywhere in
-// the kernel, made the fixed-point adjoint about a tenth slower).
+// FM (adjoint only) picks the chunks a call runs: kFmFixed only those that
+// accumulate in fixed point, kFmFloat only the others (non-finite values, or
+// a scale outside the safe range; see the top of the file), with float
+// strips.  A launch of each covers every chunk, and the fixed-point kernel
+// carries no second copy of the line code (a second inlined copy, or a call
+// anywhere in the kernel, made the fixed-point adjoint about a tenth
+// slower).  The forward takes kFmAll.
 template <int DEG, bool ADJ, int RM = kRecNone, int FM = kFmAll>
 __device__ __forceinline__ bool strip_chunk(unsigned char *smem, const GridDev g, const LinesDev L,
                                             const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
@@ -607,17 +600,11 @@ __device__ __forceinline__ bool strip_chunk(unsigned char *smem, const GridDev g
         }
         __syncthreads();
         const bool fx = misc[5] != 0;
+        static_assert(!ADJ || FM != kFmAll, "the adjoint runs as fixed-point and float launches");
         if constexpr (FM == kFmFixed) {
             if (!fx) return false;   // left to the float launch
         } else if constexpr (FM == kFmFloat) {
             if (fx) return false;    // done by the fixed-point launch
-        } else {
-            if (!fx) {
-                __syncthreads();
-                strip_chunk_float_adj<DEG, RM>(smem, g, L, hdr, tabs, sino, out, outT, chunks_per_view, vec, err,
-                                               chunk, rec, rec_cap);
-                return true;
-            }
         }
     }
 
@@ -904,17 +891,6 @@ __device__ __forceinline__ bool strip_chunk(unsigned char *smem, const GridDev g
         if ((int)threadIdx.x < nl) sino[my_line] = g.h * line_acc[threadIdx.x];   // warp 0: lane = line
     }
     return true;
-}
-
-template <int DEG, int RM>
-__device__ __noinline__ void strip_chunk_float_adj(unsigned char *smem, const GridDev g, const LinesDev L,
-                                                   const LineHdr *__restrict__ hdr, const float *__restrict__ tabs,
-                                                   float *__restrict__ sino, float *__restrict__ out,
-                                                   float *__restrict__ outT, int chunks_per_view, int vec, int *err,
-                                                   int chunk, unsigned char *rec, long long rec_cap)
-{
-    strip_chunk<DEG, true, RM, kFmFloat>(smem, g, L, hdr, tabs, nullptr, nullptr, sino, out, outT, chunks_per_view,
-                                         vec, err, chunk, rec, rec_cap);
 }
 
 // One CTA per chunk.  The adjoint runs the fixed-point chunks (FM kFmFixed:
