@@ -270,6 +270,26 @@ def oracle_sample(wl, nf: int = 6000, npix: int = 160, threads: int = 0):
             "seconds": tf + ta}
 
 
+def oracle_small_full(threads: int):
+    """The FP64 oracle's whole forward and adjoint on the 64 x 64 linear
+    parallel workload (8,640 lines), timed on `threads` host cores."""
+    import numpy as np
+    import oracle
+    import workloads
+    wl = workloads.workload("parallel64_linear")
+    geo = wl.geometry
+    th, yy = oracle.lines_parallel(geo.view_angle.astype(np.float64), geo.n_det, geo.det0, geo.ddet)
+    g = oracle.Grid(wl.n, wl.n, wl.degree, wl.h)
+    t0 = time.perf_counter()
+    s = oracle.forward(g, wl.coef, th, yy, threads=threads)
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.adjoint(g, s, th, yy, threads=threads)
+    ta = time.perf_counter() - t0
+    return {"workload": "parallel64_linear (64x64 linear, 90 x 96 lines), whole forward and adjoint",
+            "cores": threads, "fwd_s": tf, "adj_s": ta, "mrays_per_s": th.size / (tf + ta) / 1e6}
+
+
 def cg_oracle_sample(sp, dev, n=64, iters=100):
     """CPU baseline of the reconstruction step, and the GPU iterates against
     it: FP64 oracle CGLS (100 iterations) on the 64 x 64 crop of the 512^2
@@ -691,6 +711,7 @@ def run_ours(args, rank, ws, local):
             line["cg"]["vs_oracle_cgls"] = cg_oracle_sample(sp, dev)
         one = oracle_sample(wl, nf=4000, npix=60, threads=1)   # ~5 s on one core
         cb["one_core"] = {"value": one["value"], "sample": one["sample"]}
+        cb["small_full"] = [oracle_small_full(ncpu), oracle_small_full(1)]
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
 
