@@ -44,8 +44,11 @@ sp_status sp_conv3x3_bwd_data(int32_t B, int32_t H, int32_t W, int32_t cin, int3
 /* Weight gradient: dw[o,ky,kx,i] = sum_{b,h,w} g[b,h,w,o] x[b,h+(ky-1)d,w+(kx-1)d,i]
  * (FP32 [cout][3][3][cin], overwritten) and dbias[o] = sum g[b,h,w,o]
  * (FP32 [cout], overwritten).  x BF16 [B][H][W][cin], g FP32.  32 -> 32 runs
- * on the tensor cores (g rounded to BF16 in dw, FP32 accumulation; dbias
- * from g in FP32); the others on the CUDA cores in FP32. */
+ * on the tcgen05 tensor cores (g rounded to BF16 in dw, FP32 accumulation in
+ * tensor memory, one atomic add per entry and block, so the order of the
+ * blocks' partial sums may vary between runs; dbias from g in FP32); the
+ * others on the CUDA cores in FP32.  Returns SP_EINVAL for unsupported
+ * channels, a dilation outside 1..16 or NULL pointers. */
 sp_status sp_conv3x3_bwd_weight(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,
                                 int32_t dilation, const void *x, const float *g, float *dw, float *dbias,
                                 void *stream);

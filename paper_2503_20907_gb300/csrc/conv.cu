@@ -16,10 +16,11 @@
 //     the input gradient is the same tcgen05 kernel run on the incoming
 //     gradient g (rounded to BF16 while it is staged) with the weights
 //     flipped while they are staged (W'[i, 8 - tap, o] = W[o, tap, i]), FP32
-//     output gated by the ReLU of the layer below; the weight gradient is a
-//     GEMM over the pixels (M = 32 output channels, N = 9 taps x 32 input
-//     channels, K = pixels) with g and x staged transposed, on mma.sync
-//     (m16n8k16), one partial sum per block added to the result.
+//     output gated by the ReLU of the layer below; the weight gradient
+//     (conv32_wgrad_tc05_kernel) is a tcgen05 GEMM over the pixels (M = 4
+//     taps x 32 input channels per tile, N = 32 output channels, K = pixels)
+//     with g and the nine shifted inputs staged transposed, one partial sum
+//     per block added to the result.
 //   gradients of the 1 -> 32 and 32 -> 1 layers: CUDA cores in FP32.
 #include <cuda_bf16.h>
 
@@ -36,16 +37,6 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int kC = 32;              // channels of the inner layers
 constexpr int kMaxDil = 16;         // largest dilation of the taps
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
 
 __device__ __forceinline__ float ld_act(const bf16 *p) { return __bfloat162float(*p); }
 
@@ -194,101 +185,6 @@ __global__ void conv_wgrad_kernel(const bf16 *__restrict__ x, const float *__res
     } else if (j < nblk + cout) {
         atomicAdd(db + (j - nblk), bacc);
     }
-}
-
-// Weight gradient of a 32 -> 32 layer on the tensor cores:
-//   dW[o, tap, i] += sum_p g[p, o] x[p + off(tap), i],  dbias[o] += sum_p g[p, o]
-// as a GEMM with M = o (two 16-row tiles), N = (tap, i) (36 tiles of 8), K =
-// pixels.  A block takes `rows` image rows (over B*H), each in chunks of
-// kWgPix pixels: the chunk of g, rounded to BF16, transposed to [o][p], and
-// for each of the nine taps the shifted chunk of x transposed to [i][p]
-// (zero outside the image), so that every fragment is a pair of consecutive
-// pixels.  Warp w owns N tiles 9w..9w+8 of both M tiles (72 accumulators
-// per thread); the block adds its partial sums to dw and dbias at the end.
-constexpr int kWgPix = 64;                // pixels per staged chunk
-constexpr int kWgStride = kWgPix + 8;     // bf16 per staged channel row (conflict-free fragment loads)
-
-__global__ void __launch_bounds__(128) conv32_wgrad_kernel(const bf16 *__restrict__ x, const float *__restrict__ g,
-                                                           float *__restrict__ dw, float *__restrict__ db, int B,
-                                                           int H, int W, int rows, int dil)
-{
-    __shared__ __align__(16) bf16 gs[kC][kWgStride];          // g^T of the chunk
-    __shared__ __align__(16) bf16 xs[9][kC][kWgStride];       // x^T shifted by each tap
-    __shared__ float bsum[kC];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gq = lane >> 2, t = lane & 3;
-    float acc[2][9][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int n = 0; n < 9; ++n)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[mt][n][k] = 0.f;
-    if (threadIdx.x < kC) bsum[threadIdx.x] = 0.f;
-    float bpart = 0.f;   // dbias of channel (threadIdx.x & 31), partial
-    const int r0 = blockIdx.x * rows, r1 = min(r0 + rows, B * H);
-    for (int r = r0; r < r1; ++r) {
-        const int bb = r / H, hh = r - bb * H;
-        for (int c0 = 0; c0 < W; c0 += kWgPix) {
-            __syncthreads();
-            // g chunk: thread (channel o = tid & 31, pixel group) reads along pixels
-            for (int k = threadIdx.x; k < kC * kWgPix; k += 128) {
-                const int o = k & 31, pp = k >> 5;
-                const int ww = c0 + pp;
-                const float v = ww < W ? g[(((size_t)bb * H + hh) * W + ww) * kC + o] : 0.f;
-                gs[o][pp] = __float2bfloat16(v);
-                bpart += v;
-            }
-            // x chunks for the nine taps: xs[tap][i][pp] = x[hh + (ky-1)d, c0 + pp + (kx-1)d, i]
-            for (int k = threadIdx.x; k < 9 * kC * kWgPix; k += 128) {
-                const int i = k & 31, rem = k >> 5, pp = rem % kWgPix, tap = rem / kWgPix;
-                const int y0 = hh + (tap / 3 - 1) * dil, x0 = c0 + pp + (tap % 3 - 1) * dil;
-                xs[tap][i][pp] = (y0 >= 0 && y0 < H && x0 >= 0 && x0 < W)
-                                     ? x[(((size_t)bb * H + y0) * W + x0) * kC + i]
-                                     : __float2bfloat16(0.f);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int kc = 0; kc < kWgPix; kc += 16) {
-                uint32_t a[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int m = mt * 16 + gq;
-                    a[mt][0] = *reinterpret_cast<const uint32_t *>(&gs[m][kc + 2 * t]);
-                    a[mt][1] = *reinterpret_cast<const uint32_t *>(&gs[m + 8][kc + 2 * t]);
-                    a[mt][2] = *reinterpret_cast<const uint32_t *>(&gs[m][kc + 2 * t + 8]);
-                    a[mt][3] = *reinterpret_cast<const uint32_t *>(&gs[m + 8][kc + 2 * t + 8]);
-                }
-#pragma unroll
-                for (int n = 0; n < 9; ++n) {
-                    const int nt = warp * 9 + n;           // N tile: tap nt / 4, channels 8 (nt % 4)..
-                    const int tap = nt >> 2, i = (nt & 3) * 8 + gq;
-                    const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&xs[tap][i][kc + 2 * t]);
-                    const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&xs[tap][i][kc + 2 * t + 8]);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt)
-                        mma_bf16(acc[mt][n], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
-                }
-            }
-        }
-    }
-    // accumulator (mt, n): rows o = 16 mt + gq (+8), columns N = 8 nt + 2t (+1)
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int n = 0; n < 9; ++n) {
-            const int nt = warp * 9 + n, tap = nt >> 2, i = (nt & 3) * 8 + 2 * t;
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int o = mt * 16 + gq + 8 * half;
-                float *d = dw + ((size_t)o * 9 + tap) * kC + i;
-                atomicAdd(d, acc[mt][n][2 * half]);
-                atomicAdd(d + 1, acc[mt][n][2 * half + 1]);
-            }
-        }
-    atomicAdd(&bsum[threadIdx.x & 31], bpart);
-    __syncthreads();
-    if (threadIdx.x < kC) atomicAdd(db + threadIdx.x, bsum[threadIdx.x]);
 }
 
 // W'[i, 2-ky, 2-kx, o] = W[o, ky, kx, i] (the input gradient as a forward convolution)
@@ -519,6 +415,206 @@ __global__ void __launch_bounds__(128) conv32_tc05_kernel(const void *__restrict
     }
 }
 
+// The 32 -> 32 weight gradient on tcgen05:
+//   dW[o, tap, i] = sum_p g[p, o] x[p + off(tap), i],  dbias[o] = sum_p g[p, o]
+// taken as D[(tap, i)][o] = sum over pixels p of A[(tap, i)][p] B[o][p]: M =
+// 4 taps x 32 input channels per MMA tile (three tiles; tap slots 9..11 are
+// zero), N = the 32 output channels, K = pixels, 16 per MMA.  A block takes
+// `rows` image rows (over B*H), each in segments of 128 pixels, thread p
+// staging pixel p of the segment: for A, per 8-pixel block, the nine
+// shifted inputs as [tap slot][i][8 pixels] (K-major core matrices: LBO one
+// pixel block, SBO 8 rows); for B, g rounded to BF16 as [o][8 pixels] (LBO
+// 32 x 16 B, SBO 8 rows).  One thread issues the segment's 8 K-steps x 3
+// tiles into 96 tensor-memory columns, and the block waits for them
+// (bounded) before it stages the next segment.  At the end warp w reads the
+// accumulators of taps 4t + w and the block adds them, and its FP32 sums of
+// g, to dw and dbias with one atomic per entry; a block whose MMAs did not
+// complete adds NaN.
+constexpr int kWgSlots5 = 12;                          // tap slots: 9 taps, 3 zero
+constexpr int kWgBlockA5 = kWgSlots5 * kC * 16;        // A bytes per 8-pixel block (6,144)
+constexpr int kWgABytes5 = (kTile5 / 8) * kWgBlockA5;  // 98,304
+constexpr int kWgBBytes5 = (kTile5 / 8) * kC * 16;     // 8,192
+constexpr int kWgSmem5 = kWgABytes5 + kWgBBytes5 + 16; // + mbarrier and TMEM address
+constexpr uint32_t kWgCols5 = 128;                     // 3 tiles x 32 columns, as a power of two
+
+// Writes the 32 channels of one pixel, v[k] = channels 8k..8k+7 as BF16
+// pairs, into the rows c = 0..31 (16-byte pitch) of its column `col` of a
+// staged [channel][8 pixels] block.  The four 8-pixel blocks of a warp
+// write with their word order rotated by rot = 0..3, so that a store
+// instruction of the warp meets 16 distinct banks.
+__device__ __forceinline__ void stage_column(unsigned short *col, const uint4 (&v)[4], int rot)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t a0 = v[k].x, a1 = v[k].y, a2 = v[k].z, a3 = v[k].w;
+        if (rot & 1) { const uint32_t t = a0; a0 = a1; a1 = a2; a2 = a3; a3 = t; }
+        if (rot & 2) { uint32_t t = a0; a0 = a2; a2 = t; t = a1; a1 = a3; a3 = t; }
+        const uint32_t q[4] = {a0, a1, a2, a3};   // q[m] = channels 8k + 2((m + rot) & 3) (+1)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int c = 8 * k + 2 * ((m + rot) & 3);
+            col[c * 8] = (unsigned short)(q[m] & 0xFFFFu);
+            col[(c + 1) * 8] = (unsigned short)(q[m] >> 16);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) conv32_wgrad_tc05_kernel(const bf16 *__restrict__ x,
+                                                                const float *__restrict__ g, float *__restrict__ dw,
+                                                                float *__restrict__ db, int B, int H, int W,
+                                                                int rows, int dil)
+{
+    extern __shared__ __align__(128) unsigned char smw[];
+    unsigned char *as = smw;
+    unsigned char *bs = smw + kWgABytes5;
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(smw + kWgABytes5 + kWgBBytes5);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pb = threadIdx.x >> 3, pc = threadIdx.x & 7;   // this thread's pixel: block, column
+    const int rot = pb & 3;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(tslot)),
+                     "r"(kWgCols5)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // tap slots 9..11 of every pixel block stay zero
+    for (int k = threadIdx.x; k < (kTile5 / 8) * (kWgSlots5 - 9) * kC; k += 128) {
+        const int blk = k / ((kWgSlots5 - 9) * kC), rem = k - blk * (kWgSlots5 - 9) * kC;
+        *reinterpret_cast<uint4 *>(as + blk * kWgBlockA5 + (9 * kC + rem) * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = *tslot;
+
+    float gsum[kC];   // FP32 sums of g over this thread's pixels (bias gradient)
+#pragma unroll
+    for (int o = 0; o < kC; ++o) gsum[o] = 0.f;
+    const int r0 = blockIdx.x * rows, r1 = min(r0 + rows, B * H);
+    const int segs = (W + kTile5 - 1) / kTile5;
+    bool done = true;
+    uint32_t nseg = 0;
+    for (int r = r0; r < r1 && done; ++r) {
+        const int b = r / H, h = r - b * H;
+        for (int sg = 0; sg < segs && done; ++sg, ++nseg) {
+            const int ww = sg * kTile5 + threadIdx.x;
+            // B: g of this pixel in BF16 (zero past the row)
+            {
+                uint4 v[4] = {};
+                if (ww < W) {
+                    const float4 *gp = reinterpret_cast<const float4 *>(g + (((size_t)b * H + h) * W + ww) * kC);
+                    uint32_t *vw = reinterpret_cast<uint32_t *>(v);
+#pragma unroll
+                    for (int k = 0; k < kC / 4; ++k) {
+                        const float4 f = gp[k];
+                        gsum[4 * k] += f.x; gsum[4 * k + 1] += f.y; gsum[4 * k + 2] += f.z; gsum[4 * k + 3] += f.w;
+                        const __nv_bfloat162 lo = __floats2bfloat162_rn(f.x, f.y), hi = __floats2bfloat162_rn(f.z, f.w);
+                        vw[2 * k] = *reinterpret_cast<const uint32_t *>(&lo);
+                        vw[2 * k + 1] = *reinterpret_cast<const uint32_t *>(&hi);
+                    }
+                }
+                stage_column(reinterpret_cast<unsigned short *>(bs + pb * kC * 16) + pc, v, rot);
+            }
+            // A: the nine shifted inputs of this pixel (zero outside the image)
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int ky = tap / 3, kx = tap - 3 * ky;
+                const int hh = h + (ky - 1) * dil, wx = ww + (kx - 1) * dil;
+                uint4 v[4] = {};
+                if (ww < W && hh >= 0 && hh < H && wx >= 0 && wx < W) {
+                    const uint4 *xp = reinterpret_cast<const uint4 *>(x + (((size_t)b * H + hh) * W + wx) * kC);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) v[k] = xp[k];
+                }
+                stage_column(reinterpret_cast<unsigned short *>(as + pb * kWgBlockA5 + tap * kC * 16) + pc, v, rot);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                constexpr uint32_t idesc = umma_idesc_bf16(kTile5, kC);
+                const uint32_t abase = s_u32(as), bbase = s_u32(bs);
+#pragma unroll 1
+                for (int k = 0; k < kTile5 / 16; ++k) {
+                    const uint64_t bdesc = umma_smem_desc(bbase + (uint32_t)(2 * k * kC * 16), kC * 16, 128);
+#pragma unroll 1
+                    for (int t = 0; t < 3; ++t) {
+                        const uint64_t adesc =
+                            umma_smem_desc(abase + (uint32_t)(2 * k * kWgBlockA5 + 4 * t * kC * 16), kWgBlockA5, 128);
+                        const uint32_t accumulate = (nseg > 0 || k > 0) ? 1u : 0u;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                         taddr + (uint32_t)(t * kC)),
+                                     "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+                                     : "memory");
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 s_u32(mbar))
+                             : "memory");
+            }
+            // bounded wait for the segment's MMAs before its operands are overwritten
+            bool ok_seg = false;
+            for (int it = 0; it < (1 << 24) && !ok_seg; ++it) {
+                uint32_t ok;
+                asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                             "selp.u32 %0, 1, 0, p;\n\t}"
+                             : "=r"(ok)
+                             : "r"(s_u32(mbar)), "r"(nseg & 1u)
+                             : "memory");
+                ok_seg = ok != 0;
+            }
+            done = __syncthreads_and(ok_seg) != 0;   // block-uniform: stop at the first failure
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+    }
+    const float bad = __int_as_float(0x7fc00000);
+    // bias gradient: the warp's sums, one atomic per channel and warp
+#pragma unroll
+    for (int o = 0; o < kC; ++o) {
+        float v = gsum[o];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) atomicAdd(db + o, done ? v : bad);
+    }
+    // weight gradient: warp w holds the rows (tap 4t + w, i = lane) of tile t
+#pragma unroll 1
+    for (int t = 0; t < 3; ++t) {
+        uint32_t acc[kC];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                     "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, "
+                     "%31}, [%32];"
+                     : "=r"(acc[0]), "=r"(acc[1]), "=r"(acc[2]), "=r"(acc[3]), "=r"(acc[4]), "=r"(acc[5]),
+                       "=r"(acc[6]), "=r"(acc[7]), "=r"(acc[8]), "=r"(acc[9]), "=r"(acc[10]), "=r"(acc[11]),
+                       "=r"(acc[12]), "=r"(acc[13]), "=r"(acc[14]), "=r"(acc[15]), "=r"(acc[16]), "=r"(acc[17]),
+                       "=r"(acc[18]), "=r"(acc[19]), "=r"(acc[20]), "=r"(acc[21]), "=r"(acc[22]), "=r"(acc[23]),
+                       "=r"(acc[24]), "=r"(acc[25]), "=r"(acc[26]), "=r"(acc[27]), "=r"(acc[28]), "=r"(acc[29]),
+                       "=r"(acc[30]), "=r"(acc[31])
+                     : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * kC)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int tap = 4 * t + warp;
+        if (tap < 9 && nseg > 0) {
+#pragma unroll
+            for (int o = 0; o < kC; ++o)
+                atomicAdd(dw + ((size_t)o * 9 + tap) * kC + lane, done ? __uint_as_float(acc[o]) : bad);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kWgCols5)
+                     : "memory");
+    }
+}
+
 }  // namespace
 }  // namespace spx
 
@@ -606,11 +702,20 @@ sp_status sp_conv3x3_bwd_weight(int32_t B, int32_t H, int32_t W, int32_t cin, in
     cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * (size_t)cout * 9 * cin, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dbias, 0, sizeof(float) * (size_t)cout, s);
     if (cin == 32 && cout == 32) {
+        // about two blocks per SM (each holds 104 KB of shared memory), every
+        // block at least one image row
+        int dev = 0, sms = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(spx::conv32_wgrad_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     spx::kWgSmem5);
         if (e == cudaSuccess) {
-            const int rows = 16;
-            const int blocks = (B * H + rows - 1) / rows;
-            spx::conv32_wgrad_kernel<<<blocks, 128, 0, s>>>(static_cast<const spx::bf16 *>(x), g, dw, dbias, B, H, W,
-                                                            rows, dilation);
+            const int64_t nrows = (int64_t)B * H, target = 2 * (int64_t)(sms > 0 ? sms : 1);
+            const int rows = (int)((nrows + target - 1) / target);
+            const int blocks = (int)((nrows + rows - 1) / rows);
+            spx::conv32_wgrad_tc05_kernel<<<blocks, 128, spx::kWgSmem5, s>>>(static_cast<const spx::bf16 *>(x), g, dw,
+                                                                             dbias, B, H, W, rows, dilation);
             e = cudaGetLastError();
         }
         return e == cudaSuccess ? SP_OK : spx::record_error(SP_ECUDA, cudaGetErrorString(e));

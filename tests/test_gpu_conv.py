@@ -3,7 +3,7 @@ against the FP64 oracle layers on BF16-exact inputs: the forward (tcgen05
 tensor cores for 32 -> 32, CUDA cores for the edge layers, ragged tiles of
 128 pixels), both gradients, the autograd wrapper, and exact integer sums
 that pin the tensor-core operand layouts (shared-memory descriptors, tensor
-memory lanes)."""
+memory lanes) of the forward and of the weight gradient."""
 import numpy as np
 import pytest
 
@@ -95,6 +95,28 @@ def test_conv_gradients_match_oracle(cin, cout, d, W):
                                         dx.data_ptr(), None))
     ref_x = conv3x3_grad_input(g_in, _exact(w), d=d) * (_exact(gate) > 0)
     assert np.linalg.norm(dx.cpu().numpy() - ref_x) / np.linalg.norm(ref_x) < 1e-5
+
+
+@pytest.mark.parametrize("B,H,W,d", [(1, 3, 33, 1), (2, 35, 129, 16), (1, 4, 256, 1), (2, 5, 300, 5),
+                                     (3, 200, 20, 2), (1, 1, 1, 1)])
+def test_conv32_weight_gradient_exact_integer_sums(B, H, W, d):
+    # small integers in x and g: every product and sum is exact in FP32, so
+    # the tensor-core weight gradient (taps x input channels as M, pixels as
+    # K, several 128-pixel segments and blocks of several rows) must equal
+    # the definition bit for bit
+    from paper_2503_20907_gb300 import _lib
+    rng = np.random.default_rng(B * 1000 + H * W + d)
+    x = rng.integers(-2, 3, size=(B, H, W, 32)).astype(np.float32)
+    g = rng.integers(-2, 3, size=(B, H, W, 32)).astype(np.float32)
+    dw = torch.empty((32, 3, 3, 32), device=DEV)
+    db = torch.empty(32, device=DEV)
+    gd = torch.from_numpy(g).to(DEV)
+    _lib._check(_lib.load().sp_conv3x3_bwd_weight(B, H, W, 32, 32, d, _bf16(x).data_ptr(), gd.data_ptr(),
+                                                  dw.data_ptr(), db.data_ptr(), None))
+    ref_w, ref_b = conv3x3_grad_weight(x.astype(np.float64), g.astype(np.float64), d=d)
+    assert np.abs(ref_w).max() < 2 ** 24
+    assert np.array_equal(dw.cpu().numpy().astype(np.float64), ref_w)
+    assert np.array_equal(db.cpu().numpy().astype(np.float64), ref_b)
 
 
 def test_flip_weights():
