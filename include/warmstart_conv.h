@@ -48,7 +48,8 @@ sp_status sp_conv3x3_bwd_data(int32_t B, int32_t H, int32_t W, int32_t cin, int3
  * tensor memory, one atomic add per entry and block, so the order of the
  * blocks' partial sums may vary between runs; dbias from g in FP32); the
  * others on the CUDA cores in FP32.  Returns SP_EINVAL for unsupported
- * channels, a dilation outside 1..16 or NULL pointers. */
+ * channels, a dilation outside 1..16, NULL pointers, or (32 -> 32) x or g
+ * not 16-byte aligned. */
 sp_status sp_conv3x3_bwd_weight(int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,
                                 int32_t dilation, const void *x, const float *g, float *dw, float *dbias,
                                 void *stream);

@@ -698,6 +698,8 @@ sp_status sp_conv3x3_bwd_weight(int32_t B, int32_t H, int32_t W, int32_t cin, in
     if (!((cin == 32 && (cout == 32 || cout == 1)) || (cin == 1 && cout == 32)))
         return spx::record_error(SP_EINVAL, "supported channels: 1->32, 32->32, 32->1");
     if (!x || !g || !dw || !dbias) return spx::record_error(SP_EINVAL, "NULL pointer");
+    if (cin == 32 && cout == 32 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(g)) & 15))
+        return spx::record_error(SP_EINVAL, "x, g must be 16-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * (size_t)cout * 9 * cin, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dbias, 0, sizeof(float) * (size_t)cout, s);

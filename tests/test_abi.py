@@ -90,3 +90,31 @@ def test_plan_and_batch_host_side_checks(lib):
     assert lib.spline_batch_autotune(None, None, None, None, None) == L.SP_EINVAL
     assert lib.spline_batch_destroy(None) == L.SP_OK
     assert lib.spline_plan_set_paths(None, 0, 0) == L.SP_EINVAL
+
+
+def test_conv_host_side_argument_checks(lib):
+    # every case returns SP_EINVAL before any CUDA call (the pointers are
+    # never dereferenced): sizes, dilation, channel pairs, NULL and
+    # misaligned pointers of the tensor-core layers
+    from paper_2503_20907_gb300 import _lib as L
+    P = 4096                                             # a 16-byte aligned dummy address
+    for args in [(0, 4, 4, 32, 32, 1), (1, 0, 4, 32, 32, 1), (1, 4, 4, 32, 32, 0), (1, 4, 4, 32, 32, 17),
+                 (1, 4, 4, 16, 32, 1), (1, 4, 4, 32, 8, 1), (1, 4, 4, 1, 1, 1)]:
+        assert lib.sp_conv3x3_fwd(*args, P, P, None, 0, P, None) == L.SP_EINVAL, args
+        assert lib.sp_conv3x3_bwd_data(*args, P, P, None, P, None) == L.SP_EINVAL, args
+        assert lib.sp_conv3x3_bwd_weight(*args, P, P, P, P, None) == L.SP_EINVAL, args
+    ok = (2, 4, 4, 32, 32, 1)
+    assert lib.sp_conv3x3_fwd(*ok, None, P, None, 0, P, None) == L.SP_EINVAL
+    assert b"NULL" in lib.sp_last_error()
+    assert lib.sp_conv3x3_fwd(*ok, P + 8, P, None, 0, P, None) == L.SP_EINVAL
+    assert b"aligned" in lib.sp_last_error()
+    assert lib.sp_conv3x3_bwd_data(*ok, P + 4, P, None, P, None) == L.SP_EINVAL
+    assert b"aligned" in lib.sp_last_error()
+    assert lib.sp_conv3x3_bwd_data(*ok, P, P, P + 2, P, None) == L.SP_EINVAL     # gate
+    assert b"aligned" in lib.sp_last_error()
+    assert lib.sp_conv3x3_bwd_weight(*ok, P + 2, P, P, P, None) == L.SP_EINVAL
+    assert b"aligned" in lib.sp_last_error()
+    assert lib.sp_conv3x3_bwd_weight(*ok, P, P + 8, P, P, None) == L.SP_EINVAL
+    assert lib.sp_conv3x3_bwd_weight(*ok, P, P, None, P, None) == L.SP_EINVAL
+    assert lib.sp_conv3x3_flip_weights(0, 32, P, P, None) == L.SP_EINVAL
+    assert lib.sp_conv3x3_flip_weights(32, 32, None, P, None) == L.SP_EINVAL
