@@ -333,7 +333,7 @@ sp_status spline_plan_destroy(sp_plan *plan);
  * count in sp_last_error().  The first call with a nonempty line list on a
  * device looks up the array's device address (cudaGetSymbolAddress); under
  * lazy module loading (CUDA_MODULE_LOADING=LAZY, PyTorch's default) that
- * lookup is also when the driver loads the array and reserves its 48 MiB on
+ * lookup is also when the CUDA driver loads the array and reserves its 48 MiB on
  * that device (and the kernels' code).  So make one such call first (a
  * one-line list suffices), before the rest of the device memory goes to the
  * caller's own pool and before any stream capture; later calls take no

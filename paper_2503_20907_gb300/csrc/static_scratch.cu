@@ -16,7 +16,7 @@
 // When that array takes device memory: the library is built without
 // relocatable device code, so the array sits in a module of its own, and
 // under lazy module loading (CUDA_MODULE_LOADING=LAZY, which PyTorch turns
-// on) the driver loads that module, and reserves the array's 48 MiB, only at
+// on) the CUDA driver loads that module, and reserves the array's 48 MiB, only at
 // the first cudaGetSymbolAddress on a device, i.e. during the first call of
 // this entry point there.  That first call (a one-line list suffices) is
 // therefore the one step that takes device memory; callers make it before
